@@ -1,0 +1,200 @@
+/*
+ * fpssft.h -- C ABI of the FPS-SFT recovery loop on GB300 (sm_103a).
+ *
+ * FPS-SFT (Wang, Patel, Petropulu, arXiv 1711.11407) recovers the K on-grid D-D complex sinusoids
+ * of a cube x(n) = sum_k a_k exp(j 2 pi sum_d k_d n_d / N_d)  (Sec. 2, Eq. sigModel2; D-D in
+ * Sec. 2.3) from samples taken along discrete lines.  Every iteration t uses one slope alpha_t
+ * and one offset tau_t (both in X_D = [N_0] x ... x [N_{D-1}]) and D+1 lines of length
+ * L = LCM(N_0, ..., N_{D-1}) (Lemma 1):
+ *     line 0:    s_0(l)     = x([alpha l + tau]_N)                 (Eq. sample_slice)
+ *     line d+1:  s_{d+1}(l) = x([alpha l + tau + e_d]_N)           (Sec. 2.3; D+1 lines)
+ * their L-point DFTs  s_hat_j(m) = (1/L) sum_l s_j(l) exp(-j 2 pi l m / L)   (Eq. hs),
+ * subtracts the bins of the sinusoids recovered so far (construction-subtraction, Sec. 2.2, done
+ * on the bins), decodes every 1-sparse bin by the OFDM trick (Eq. decoding) and merges the
+ * result into the recovered set.
+ *
+ * Conventions shared by every call:
+ *   - Complex numbers are complex64: two floats (re, im), interleaved.
+ *   - A batch holds `batch` cubes with per-signal shapes dims[b][0..D-1] (1 <= D <= 4).  Cubes are
+ *     C-order (last dimension fastest) and concatenated in one device buffer; offsets[b] (int64,
+ *     device) is the element offset of cube b.
+ *   - L_b = LCM of signal b's dims; L_max = max_b L_b.  Bin and line arrays are
+ *     [batch][n_sched][D+1][L_max] complex64; entries m >= L_b of a line are written as zero.
+ *   - Schedules alpha, tau are int32 [batch][n_sched][D] (device) with 0 <= alpha_d, tau_d < N_d.
+ *     fpssft_recover reads [batch][T_max][D], where T_max is reported by fpssft_plan_get_info.
+ *   - Recovered sets are k: int32 [batch][k_cap][D] (frequency indices), a: complex64
+ *     [batch][k_cap], count: int32 [batch].
+ *   - Device pointers are plain CUDA device addresses; `stream` is a cudaStream_t (NULL = legacy
+ *     default stream).  All calls except plan creation/destruction and fpssft_recover_host are
+ *     asynchronous on `stream`; they allocate nothing and synchronise nothing, so they can be
+ *     recorded into a CUDA graph.
+ *   - Ownership: the caller owns every buffer it passes.  The plan owns its own device workspace
+ *     (shape table, twiddle tables, work queue, host staging buffers) and frees it in
+ *     fpssft_plan_destroy.
+ *   - Errors: the return code reports argument validation and launch errors; the message of the
+ *     last failure on the calling thread is returned by fpssft_last_error.  Errors found on the
+ *     device (recovered-set capacity) are written per signal to out_status after the stream
+ *     completes.  No call traps or aborts on the device.
+ */
+#ifndef FPSSFT_H
+#define FPSSFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FPSSFT_OK = 0,
+  FPSSFT_ERR_INVALID = 1,      /* bad argument: null pointer, dims out of range, bad mode */
+  FPSSFT_ERR_CUDA = 2,         /* a CUDA runtime call failed (message names it) */
+  FPSSFT_ERR_ALLOC = 3,        /* the plan could not allocate its workspace */
+  FPSSFT_ERR_CAPACITY = 4,     /* per signal, in out_status: the recovered set reached k_cap */
+  FPSSFT_ERR_TIMEOUT = 5,      /* reserved for bounded device waits (none exist today) */
+  FPSSFT_ERR_UNSUPPORTED = 6   /* valid but not implemented: L too long for shared memory, ... */
+} fpssft_status;
+
+/* Recovery parameters.  The thresholds implement the 1-sparsity test the paper leaves open
+ * (Sec. 2.2 only states that a non-zero bin is 1-sparse with high probability; Sec. 2.1 tests
+ * 1-sparsity by equal magnitudes).  For every bin m, with s_j = s_hat_j(m):
+ *   T0  |s_0| > theta0;
+ *   T1  | |s_{d+1}| - |s_0| | <= rho |s_0| for every d;
+ *   T2  |u_d - floor(u_d + 1/2)| <= eta, u_d = N_d phi(s_{d+1} conj(s_0)) / (2 pi), phi in (-pi, pi];
+ *   T3  [sum_d (L/N_d) alpha_d k_d]_L = m  with k_d = [floor(u_d + 1/2)]_{N_d}  (Eq. orthogonality);
+ * a bin passing all four yields (k, a = s_0 exp(-j 2 pi sum_d k_d tau_d / N_d)) (Eq. decoding). */
+typedef struct {
+  int T;             /* iterations; 0 = per signal floor(N / ((D+1) L)), the budget of Sec. 3 */
+  int k_cap;         /* capacity of each signal's recovered set (>= 1) */
+  float theta0;      /* T0 threshold (absolute) */
+  float rho;         /* T1 relative magnitude tolerance */
+  float eta;         /* T2 distance of the decoded phase from the frequency grid */
+  int early_stop;    /* nonzero: stop a signal when no bin of line 0 passes T0 after peeling */
+  int peel_mode;     /* 0 = subtract the recovered set's projections from the bins (only mode) */
+  int threads;       /* CTA size of the recovery kernel; 0 = library default */
+  int ctas_per_sm;   /* resident CTAs per SM for the persistent recovery grid; 0 = occupancy */
+} fpssft_params;
+
+typedef struct fpssft_plan_s* fpssft_plan_t;
+
+typedef struct {
+  int D;
+  int batch;
+  int L_max;          /* longest line length in the batch */
+  int T_max;          /* schedule rows fpssft_recover reads per signal */
+  int k_cap;
+  int hash_cap;       /* open-addressing table size per signal (power of two >= 2 k_cap) */
+  int n_shapes;       /* distinct shapes in the batch */
+  int threads;        /* CTA size used by fpssft_recover */
+  int grid;           /* persistent CTAs launched by fpssft_recover */
+  int smem_bytes;     /* dynamic shared memory per recovery CTA */
+  int twiddles_in_smem;
+} fpssft_plan_info;
+
+/* Create a plan for `batch` signals of dimension D with shapes dims (HOST int64 [batch][D],
+ * each N_d >= 1).  Computes L_b = LCM(dims[b]) (Lemma 1), the mixed-radix FFT factorisation of
+ * every distinct L, FP64-derived twiddle tables, the per-signal iteration budget and a
+ * longest-first work order, and uploads them to device workspace owned by the plan.
+ * Returns FPSSFT_ERR_UNSUPPORTED when a line of the batch does not fit one CTA's shared memory.
+ * Must be called with the target device current. */
+fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch, const int64_t* dims,
+                                 const fpssft_params* params);
+
+/* Same as fpssft_plan_create (the name used by the paper-level description of this interface). */
+fpssft_status fpssft_plan(fpssft_plan_t* out, int D, int batch, const int64_t* dims,
+                          const fpssft_params* params);
+
+void fpssft_plan_destroy(fpssft_plan_t plan);
+
+fpssft_status fpssft_plan_get_info(fpssft_plan_t plan, fpssft_plan_info* info);
+
+/* Per-signal line length L_b and iteration budget T_b, written to HOST int32 arrays [batch]
+ * (either may be NULL). */
+fpssft_status fpssft_plan_get_lengths(fpssft_plan_t plan, int32_t* L_out, int32_t* T_out);
+
+/* Line projection (Eq. sample_slice + Eq. hs): for every signal b and schedule row s, the D+1
+ * line DFTs s_hat_j(m), written to bins [batch][n_sched][D+1][L_max] (complex64, device).  By the
+ * projection-slice identity (Eq. freqSum, Lemma 1) bin m of line j equals the sum, over the
+ * frequencies k with [sum_d (L/N_d) alpha_d k_d]_L = m, of the D-D DFT value at k times
+ * exp(j 2 pi sum_d k_d (tau_d + [j = d+1]) / N_d). */
+fpssft_status fpssft_project(fpssft_plan_t plan, const void* cubes, const int64_t* offsets,
+                             const int32_t* alpha, const int32_t* tau, int n_sched, void* bins,
+                             void* stream);
+
+/* Raw line samples s_j(l) (Eq. sample_slice, no DFT), same layout as fpssft_project's bins. */
+fpssft_status fpssft_lines(fpssft_plan_t plan, const void* cubes, const int64_t* offsets,
+                           const int32_t* alpha, const int32_t* tau, int n_sched, void* lines,
+                           void* stream);
+
+/* The full recovery loop (Sec. 2.2): for every signal, up to T_b iterations of gather, L-point
+ * DFT, subtraction of the recovered set's bins, 1-sparse classification + OFDM decode, merge.
+ * One persistent launch processes the whole batch (longest signals first).
+ *   alpha, tau:  int32 [batch][T_max][D] (device).
+ *   init_count:  NULL, or int32 [batch] (device): resume from the first init_count[b] entries
+ *                already present in out_k / out_a (checkpoint / teacher forcing).
+ *   out_k, out_a, out_count: the recovered set, entries with |a| <= theta0 dropped, sorted by
+ *                row-major linear frequency index.
+ *   out_iters:   iterations whose lines were sampled.
+ *   out_status:  FPSSFT_OK or FPSSFT_ERR_CAPACITY per signal.
+ * Allocates nothing; the caller's buffers and the plan's workspace are the only memory used. */
+fpssft_status fpssft_recover(fpssft_plan_t plan, const void* cubes, const int64_t* offsets,
+                             const int32_t* alpha, const int32_t* tau, const int32_t* init_count,
+                             int32_t* out_k, void* out_a, int32_t* out_count, int32_t* out_iters,
+                             int32_t* out_status, void* stream);
+
+/* fpssft_recover on HOST buffers: cubes (complex64, total elements = sum N_b), offsets, alpha,
+ * tau and init_count in host memory (pinned memory gives full copy bandwidth).  The call copies
+ * the inputs into plan-owned device staging (allocated on the first call), runs the recovery on
+ * `stream`, copies every output back into the host arrays and synchronises the stream before
+ * returning. */
+fpssft_status fpssft_recover_host(fpssft_plan_t plan, const void* cubes, const int64_t* offsets,
+                                  const int32_t* alpha, const int32_t* tau, const int32_t* init_count,
+                                  int32_t* out_k, void* out_a, int32_t* out_count, int32_t* out_iters,
+                                  int32_t* out_status, void* stream);
+
+/* Sparse synthesis (Eq. freqSum applied to a set {(k_i, a_i)}, the construction step of Sec. 2.2):
+ *   bins[b][s][j][m] = sum over i < count[b] with [sum_d (L/N_d) alpha_d k_{i,d}]_L = m of
+ *                      a_i exp(j 2 pi sum_d k_{i,d} (tau_d + [j = d+1]) / N_d).
+ * accumulate = 0 overwrites bins, +1 adds to them, -1 subtracts from them (the peel). */
+fpssft_status fpssft_synth(fpssft_plan_t plan, const int32_t* alpha, const int32_t* tau,
+                           int n_sched, const int32_t* k, const void* a, const int32_t* count,
+                           int accumulate, void* bins, void* stream);
+
+/* One iteration's classification, decode and merge on precomputed bins [batch][1][D+1][L_max]
+ * (already peeled), updating the set (k, a, count) in place, as in fpssft_recover.  Writes the
+ * number of line-0 bins passing T0 to t0_count [batch] and ORs FPSSFT_ERR_CAPACITY into status.
+ * Building block of the unfused, per-iteration host-driven form of the loop. */
+fpssft_status fpssft_decode(fpssft_plan_t plan, const void* bins, const int32_t* alpha,
+                            const int32_t* tau, int32_t* k, void* a, int32_t* count,
+                            int32_t* t0_count, int32_t* status, void* stream);
+
+/* Drop entries with |a| <= theta0 and sort each signal's set by linear index (in place). */
+fpssft_status fpssft_finalize(fpssft_plan_t plan, int32_t* k, void* a, int32_t* count, void* stream);
+
+typedef enum { FPSSFT_ADJ_PROJECT = 0, FPSSFT_ADJ_SYNTH = 1 } fpssft_adj_mode;
+
+/* Adjoints (conjugate transposes) of the two linear maps above.
+ *   FPSSFT_ADJ_PROJECT: grad_out (cube layout at `offsets`, complex64) += P^H grad_bins, i.e. for
+ *     every line the inverse-direction DFT scaled by 1/L,  (1/L) sum_m g_j(m) exp(+j 2 pi l m / L),
+ *     scatter-added at the line's grid points (atomic; lines may revisit a point).  k, count
+ *     unused.
+ *   FPSSFT_ADJ_SYNTH: grad_out [batch][k_cap] complex64 (overwritten for i < count[b]) =
+ *     sum over schedule rows and lines of conj(exp(j 2 pi sum_d k_{i,d}(tau_d + [j = d+1]) / N_d))
+ *     g_j(m(k_i)).  offsets unused.
+ * grad_bins: [batch][n_sched][D+1][L_max] complex64. */
+fpssft_status fpssft_adjoint(fpssft_plan_t plan, fpssft_adj_mode mode, const void* grad_bins,
+                             const int64_t* offsets, const int32_t* alpha, const int32_t* tau,
+                             int n_sched, const int32_t* k, const int32_t* count, void* grad_out,
+                             void* stream);
+
+/* Message of the last failed call on this thread ("" when none). */
+const char* fpssft_last_error(void);
+
+/* Library version string. */
+const char* fpssft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPSSFT_H */

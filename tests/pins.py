@@ -1,0 +1,341 @@
+"""Checks that pin the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each check takes the oracle module as an argument and raises AssertionError on a mismatch, so the
+same checks serve the pin tests (test_oracle_pins.py) and the planted-mistake tests
+(test_oracle_mutations.py), which patch a mistake into the oracle and expect some check to fail.
+Nothing here calls the CUDA library.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+from paper_1711_11407_gb300 import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def grid(dims):
+    return np.stack(np.meshgrid(*[np.arange(n) for n in dims], indexing="ij"), -1).reshape(-1, len(dims))
+
+
+# --- the line DFT against its definition (brute-force sum, tiny L) --------------------------------
+
+def check_line_dft_definition(O, Ls=(1, 5, 12, 30)):
+    rng = np.random.default_rng(7)
+    for L in Ls:
+        s = rng.normal(size=(2, L)) + 1j * rng.normal(size=(2, L))
+        ref = np.zeros((2, L), np.complex128)
+        for m in range(L):
+            for l in range(L):
+                ref[:, m] += s[:, l] * complex(math.cos(2 * math.pi * l * m / L), -math.sin(2 * math.pi * l * m / L))
+        ref /= L
+        got = O.line_dft(s)
+        assert np.allclose(got, ref, atol=1e-12), f"line DFT differs from Eq. hs at L={L}"
+
+
+# --- projection-slice identity (Eq. lines + Eq. freqSum vs sampling + Eq. hs) ----------------------
+
+def _fiber_rational(k, alpha, dims, L, m):
+    """Eq. lines, exactly: [sum_d k_d alpha_d / N_d - m / L]_1 == 0 in rational arithmetic."""
+    v = sum(Fraction(int(k[d]) * int(alpha[d]), int(dims[d])) for d in range(len(dims))) - Fraction(m, L)
+    return v.denominator == 1
+
+
+def _phase_rational(k, tau, dims, j):
+    v = sum(Fraction(int(k[d]) * (int(tau[d]) + (1 if j == d + 1 else 0)), int(dims[d])) for d in range(len(dims)))
+    v -= math.floor(v)
+    return complex(math.cos(2 * math.pi * v), math.sin(2 * math.pi * v))
+
+
+def check_projection_slice(O, cases=None):
+    """Every line bin equals the sum over its fibre (Eq. lines, exact rationals) of the D-D DFT
+    (numpy fftn / N) times the offset phase of Eq. freqSum."""
+    rng = np.random.default_rng(11)
+    if cases is None:
+        cases = [((6, 10), [(1, 3), (0, 1), (4, 6), (0, 0), (5, 9)]),
+                 ((4, 6, 3), [(1, 1, 1), (3, 0, 2), (2, 4, 0)]),
+                 ((5, 7), [(2, 3), (1, 0)])]
+    for dims, slopes in cases:
+        x = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+        X = np.fft.fftn(x) / x.size
+        L = math.lcm(*dims)
+        ks = grid(dims)
+        for alpha in slopes:
+            tau = [int(rng.integers(0, n)) for n in dims]
+            got = O.project(x, alpha, tau)
+            assert got.shape == (len(dims) + 1, L), "project() returns [D+1][L]"
+            for j in range(len(dims) + 1):
+                ref = np.zeros(L, np.complex128)
+                for k in ks:
+                    for m in range(L):
+                        if _fiber_rational(k, alpha, dims, L, m):
+                            ref[m] += X[tuple(k)] * _phase_rational(k, tau, dims, j)
+                            break
+                assert np.allclose(got[j], ref, atol=1e-12), f"projection-slice identity fails {dims} {alpha} line {j}"
+
+
+def check_bin_index_rational(O):
+    """Eq. orthogonality (integer form) agrees with Eq. lines (rational form) for every k."""
+    for dims in [(6, 10), (4, 6, 3), (8, 8)]:
+        L = math.lcm(*dims)
+        for alpha in [tuple(int(a) for a in al) for al in grid(dims)[::7]]:
+            ks = grid(dims)
+            m = O.bin_index(ks, alpha, dims)
+            for k, mm in zip(ks, m):
+                assert _fiber_rational(k, alpha, dims, L, int(mm)), f"bin_index wrong for k={k} alpha={alpha}"
+
+
+# --- Lemma 1: L = LCM is the shortest length with one-hot single-frequency line spectra -----------
+
+def check_lemma1_minimal(O):
+    """Orthogonal projection (Eq. orthogonal) needs every single-frequency line to close on itself
+    after L samples, for every slope: then its L-point DFT is one unit bin with no leakage.  The
+    brute-force search finds the smallest such L on tiny grids; Lemma 1 says it is LCM(N_d)."""
+    for dims in [(2, 3), (4, 6), (3, 5), (2, 2, 3), (4, 4)]:
+        N = int(np.prod(dims))
+        best = None
+        for Lp in range(1, N + 1):
+            l = np.arange(2 * Lp)
+            ok = True
+            for k in grid(dims):
+                for alpha in grid(dims):
+                    s = np.exp(2j * np.pi * sum(k[d] * ((alpha[d] * l) % dims[d]) / dims[d] for d in range(len(dims))))
+                    if not np.allclose(s[Lp:], s[:Lp], atol=1e-9):
+                        ok = False
+                        break
+                    spec = np.abs(np.fft.fft(s[:Lp]) / Lp)
+                    assert np.all((spec < 1e-9) | (np.abs(spec - 1) < 1e-9))
+                if not ok:
+                    break
+            if ok:
+                best = Lp
+                break
+        L, c = O.line_length(dims)
+        assert L == best, f"line_length{dims} = {L}, brute-force minimum is {best}"
+        assert all(cd * n == L for cd, n in zip(c, dims))
+
+
+# --- Lemma 2: uniform projection ------------------------------------------------------------------
+
+def check_uniform_projection(O):
+    found_strict = False
+    for dims in [(6, 10), (8, 8), (4, 6, 3), (12, 18)]:
+        N = int(np.prod(dims))
+        L = math.lcm(*dims)
+        ks = grid(dims)
+        slopes = grid(dims)
+        if len(slopes) > 400:
+            slopes = slopes[np.random.default_rng(3).choice(len(slopes), 400, replace=False)]
+        for alpha in slopes:
+            m = O.bin_index(ks, alpha, dims)
+            counts = np.bincount(m, minlength=L)
+            uniform = bool(np.all(counts == N // L))
+            assert O.uniform_projection(alpha, dims) == uniform, f"uniform_projection wrong at {dims} {alpha}"
+            if len(dims) == 2 and O.in_lemma2_set(alpha, dims):
+                assert uniform, f"Lemma 2: slope {alpha} in A must project uniformly on {dims}"
+            if len(dims) == 2 and uniform and not O.in_lemma2_set(alpha, dims):
+                found_strict = True
+    assert found_strict, "the uniform set should be strictly larger than Lemma 2's A somewhere"
+
+
+# --- closed-form decode of one sinusoid (Eq. decoding), every slope and offset --------------------
+
+def check_single_sinusoid(O):
+    rng = np.random.default_rng(5)
+    p = O.Params(T=1, k_cap=4)
+    for dims in [(6, 10), (5, 7), (4, 6, 3), (8, 8)]:
+        for _ in range(3):
+            k = tuple(int(rng.integers(0, n)) for n in dims)
+            a = complex(rng.normal(), rng.normal())
+            x = S.synthesize_cube(dims, np.asarray([k]), np.asarray([a]))
+            slopes = grid(dims)
+            taus = [tuple(n - 1 for n in dims), (0,) * len(dims)] + [tuple(int(rng.integers(0, n)) for n in dims) for _ in range(2)]
+            for alpha in slopes[:: max(1, len(slopes) // 40)]:
+                for tau in taus:
+                    bins = O.project(x, alpha, tau)
+                    cands, n0 = O.classify_decode(bins, alpha, tau, dims, p)
+                    assert n0 == 1 and len(cands) == 1, f"one 1-sparse bin expected {dims} {alpha} {tau}"
+                    m, kk, aa = cands[0]
+                    assert kk == k, f"decoded {kk} for planted {k} at alpha={alpha} tau={tau}"
+                    assert abs(aa - a) < 1e-12 * max(1.0, abs(a)), "decoded amplitude differs from planted"
+
+
+# --- exact recovery on tiny cubes equals the dense DFT's support ----------------------------------
+
+def check_tiny_support(O):
+    rng = np.random.default_rng(13)
+    for dims, K in [((8, 8), 4), ((12, 18), 6), ((8, 8, 8), 6), ((6, 10), 3)]:
+        for trial in range(3):
+            ss = np.random.SeedSequence([17, trial, *dims])
+            k, a, x, _, al, ta = S.make_signal(ss, dims, K, 60)
+            r = O.recover(x, al, ta, O.Params(T=60, k_cap=64))
+            X = np.fft.fftn(x) / x.size
+            supp = np.argwhere(np.abs(X) > 1e-6)
+            assert r.k.shape[0] == supp.shape[0], f"support size {r.k.shape[0]} vs dense DFT {supp.shape[0]} on {dims}"
+            assert np.array_equal(r.k, supp), f"recovered support differs from the dense DFT's on {dims}"
+            assert np.allclose(r.a, X[tuple(supp.T)], atol=1e-12), "amplitudes differ from the dense DFT"
+    del rng
+
+
+# --- construction-subtraction: bins-domain equals the literal order -------------------------------
+
+def check_peel_equivalence(O):
+    rng = np.random.default_rng(19)
+    for dims in [(8, 12), (4, 6, 3), (16, 16)]:
+        N = int(np.prod(dims))
+        k = grid(dims)[rng.choice(N, 5, replace=False)]
+        a = rng.normal(size=5) + 1j * rng.normal(size=5)
+        x = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+        for _ in range(4):
+            alpha = [int(rng.integers(0, n)) for n in dims]
+            tau = [int(rng.integers(0, n)) for n in dims]
+            s = O.sample_lines(x, alpha, tau)
+            lit = O.line_dft(O.peel_literal(s, k, a, alpha, tau, dims))
+            bins = O.peel_bins(O.line_dft(s), k, a, alpha, tau, dims)
+            assert np.allclose(lit, bins, atol=1e-12), "bins-domain peel differs from IDFT-subtract-DFT"
+
+
+# --- synthesis equals the projection of the synthesised cube --------------------------------------
+
+def check_synth_is_projection(O):
+    rng = np.random.default_rng(23)
+    for dims in [(8, 12), (4, 6, 3), (5, 7)]:
+        N = int(np.prod(dims))
+        k = grid(dims)[rng.choice(N, 6, replace=False)]
+        a = rng.normal(size=6) + 1j * rng.normal(size=6)
+        # the cube of the signal model, summed term by term (no FFT)
+        n = grid(dims)
+        x = np.zeros(N, np.complex128)
+        for kk, aa in zip(k, a):
+            x += aa * np.exp(2j * np.pi * sum(kk[d] * n[:, d] / dims[d] for d in range(len(dims))))
+        x = x.reshape(dims)
+        for _ in range(3):
+            alpha = [int(rng.integers(0, nn)) for nn in dims]
+            tau = [int(rng.integers(0, nn)) for nn in dims]
+            assert np.allclose(O.synth(k, a, alpha, tau, dims), O.project(x, alpha, tau), atol=1e-11), \
+                "synth(k, a) must equal the projection of the sinusoid cube"
+
+
+# --- adjoints -------------------------------------------------------------------------------------
+
+def check_adjoints(O):
+    rng = np.random.default_rng(29)
+    for dims in [(4, 6), (3, 4, 2), (8, 8)]:
+        N = int(np.prod(dims))
+        alpha = [int(rng.integers(0, n)) for n in dims]
+        tau = [int(rng.integers(0, n)) for n in dims]
+        P = O.project_matrix(dims, alpha, tau)
+        L = math.lcm(*dims)
+        g = rng.normal(size=(len(dims) + 1, L)) + 1j * rng.normal(size=(len(dims) + 1, L))
+        got = O.project_adjoint(g, alpha, tau, dims)
+        assert np.allclose(got.reshape(-1), P.conj().T @ g.reshape(-1), atol=1e-12), "project_adjoint != P^H"
+        x = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+        lhs = np.vdot(g.reshape(-1), O.project(x, alpha, tau).reshape(-1))
+        rhs = np.vdot(got.reshape(-1), x.reshape(-1))
+        assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs)), "dot-product test <Px, g> = <x, P^H g> fails"
+        # synthesis adjoint against the explicit matrix of synth in a
+        k = grid(dims)[rng.choice(N, 4, replace=False)]
+        Smat = np.zeros(((len(dims) + 1) * L, 4), np.complex128)
+        for i in range(4):
+            e = np.zeros(4, np.complex128)
+            e[i] = 1
+            Smat[:, i] = O.synth(k, e, alpha, tau, dims).reshape(-1)
+        ga = O.synth_adjoint(g, k, alpha, tau, dims)
+        assert np.allclose(ga, Smat.conj().T @ g.reshape(-1), atol=1e-12), "synth_adjoint != S^H"
+        # finite differences of f(x) = ||P x - y||^2 along real and imaginary directions
+        y = rng.normal(size=(len(dims) + 1, L)) + 1j * rng.normal(size=(len(dims) + 1, L))
+        f = lambda z: float(np.sum(np.abs(O.project(z, alpha, tau) - y) ** 2))
+        grad = 2 * O.project_adjoint(O.project(x, alpha, tau) - y, alpha, tau, dims)
+        h = 1e-6
+        for idx in [tuple(int(rng.integers(0, n)) for n in dims) for _ in range(3)]:
+            e = np.zeros(dims, np.complex128)
+            e[idx] = 1.0
+            dre = (f(x + h * e) - f(x - h * e)) / (2 * h)
+            dim = (f(x + 1j * h * e) - f(x - 1j * h * e)) / (2 * h)
+            assert abs(dre - grad[idx].real) < 1e-6 and abs(dim - grad[idx].imag) < 1e-6, "adjoint disagrees with FD"
+
+
+# --- Fig. 1 deadlock instance ----------------------------------------------------------------------
+
+def load_deadlock():
+    rows = read_golden("deadlock_8x8.txt")
+    dims = tuple(int(v) for v in rows[0][1:])
+    k, a, bins = [], [], {}
+    for r in rows[1:]:
+        if r[0] == "k":
+            k.append((int(r[1]), int(r[2])))
+            a.append(complex(float(r[3]), float(r[4])))
+        elif r[0] == "bins":
+            i = r.index(":")
+            bins[tuple(int(v) for v in r[1:i])] = [int(v) for v in r[i + 1:]]
+    return dims, np.asarray(k), np.asarray(a), bins
+
+
+def check_deadlock(O):
+    dims, k, a, bins = load_deadlock()
+    x = S.synthesize_cube(dims, k, a)
+    p = O.Params(T=4, k_cap=16)
+    for slope, expect in bins.items():
+        assert list(O.bin_index(k, slope, dims)) == expect, f"bins of slope {slope}"
+    # rows and columns alone: nothing can be decoded, whatever the offsets
+    for tau in [(0, 0), (3, 5), (7, 7)]:
+        for slope in [(1, 0), (0, 1)]:
+            cands, _ = O.classify_decode(O.project(x, slope, tau), slope, tau, dims, p)
+            assert cands == [], f"slope {slope} should leave no 1-sparse bin (deadlock)"
+    al = np.asarray([(1, 0), (0, 1), (1, 0), (0, 1)])
+    ta = np.asarray([(0, 0), (2, 3), (5, 1), (7, 7)])
+    r = O.recover(x, al, ta, p)
+    assert r.k.shape[0] == 0, "axis lines alone must stay in deadlock"
+    r = O.recover(x, np.asarray([(1, 1), (1, 1)]), np.asarray([(2, 5), (0, 0)]), O.Params(T=2, k_cap=16))
+    assert r.k.shape[0] == 4 and np.allclose(r.a, a[np.argsort(O.linear_index(k, dims))], atol=1e-12)
+    assert r.iters == 2, "the diagonal resolves everything in one iteration; the second finds nothing"
+
+
+# --- Fig. 3 arithmetic ---------------------------------------------------------------------------
+
+def check_fig3_samples(O):
+    rows = read_golden("fig3_mri_512x576.txt")
+    dims = tuple(int(v) for v in rows[0][1:])
+    N = dims[0] * dims[1]
+    L, _ = O.line_length(dims)
+    per_iter = (len(dims) + 1) * L / N * 100.0
+    for pct_nz, K, pct_samples in [(float(r[0]), int(r[1]), float(r[2])) for r in rows[1:]]:
+        assert abs(K / N * 100.0 - pct_nz) < 0.005 + 1e-9, "K / N matches the printed sparsity"
+        t = round(pct_samples / per_iter)
+        # the text prints one decimal, truncated or rounded (3 x 4.6875 % appears as 14.0)
+        assert t >= 1 and abs(t * per_iter - pct_samples) < 0.1, \
+            f"{pct_samples}% must be a whole number of iterations of (D+1) L samples (L = {L})"
+
+
+# --- Fig. 2 statistics -----------------------------------------------------------------------------
+
+def fig2_trials(O, K, trials, T=85, block=0, seed=0):
+    """Perfect-recovery rate and mean percentage of samples read until the set was complete."""
+    dims = (256, 256)
+    ok, pct = 0, []
+    for t in range(trials):
+        k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence([seed, K, block, t]), dims, K, T, block=block)
+        r = O.recover(x, al, ta, O.Params(T=T, k_cap=2 * K + 64), keep_history=True)
+        truth = np.sort(O.linear_index(k, dims))
+        good = r.k.shape[0] == K and np.array_equal(O.linear_index(r.k, dims), truth) and \
+            np.allclose(r.a, a[np.argsort(O.linear_index(k, dims))], atol=1e-8)
+        ok += int(good)
+        if good:
+            done = next(i + 1 for i, (n, _) in enumerate(r.history) if n >= K)
+            pct.append(done * 3 * 256 / 65536 * 100.0)
+    return ok / trials, (float(np.mean(pct)) if pct else float("nan"))

@@ -1,0 +1,135 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that some pin catches each one.
+
+A pin set that cannot tell a dropped term, a wrong sign, a wrong index or a transposed operand
+from the correct oracle would not pin it; these tests show that it can."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fpssft_oracle as O
+
+import pins
+
+CHECKS = [
+    pins.check_line_dft_definition,
+    pins.check_projection_slice,
+    pins.check_bin_index_rational,
+    pins.check_lemma1_minimal,
+    pins.check_uniform_projection,
+    pins.check_single_sinusoid,
+    pins.check_tiny_support,
+    pins.check_peel_equivalence,
+    pins.check_synth_is_projection,
+    pins.check_adjoints,
+    pins.check_deadlock,
+    pins.check_fig3_samples,
+]
+
+_orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
+
+
+def _dft_plus_sign(s):
+    return np.fft.ifft(s, axis=-1)
+
+
+def _dft_no_scale(s):
+    return np.fft.fft(s, axis=-1)
+
+
+def _points_no_shift(dims, alpha, tau):
+    p = _orig["line_points"](dims, alpha, tau)
+    return np.repeat(p[:1], p.shape[0], axis=0)
+
+
+def _points_shift_wrong_dim(dims, alpha, tau):
+    D = len(dims)
+    out = _orig["line_points"](dims, alpha, tau)
+    l = np.arange(out.shape[1])
+    for j in range(1, D + 1):
+        for d in range(D):
+            shift = 1 if (j % D) == d else 0
+            out[j, :, d] = (int(alpha[d]) * l + int(tau[d]) + shift) % int(dims[d])
+    return out
+
+
+def _bin_reversed_alpha(k, alpha, dims):
+    return _orig["bin_index"](k, list(alpha)[::-1], dims)
+
+
+def _phase_no_tau(k, tau, dims, j):
+    return _orig["line_phase"](k, [0] * len(dims), dims, j)
+
+
+def _phase_conj(k, tau, dims, j):
+    return np.conj(_orig["line_phase"](k, tau, dims, j))
+
+
+def _length_product(dims):
+    L = int(np.prod(dims))
+    return L, [L // int(n) for n in dims]
+
+
+def _length_max(dims):
+    L = max(int(n) for n in dims)
+    return L, [max(1, L // int(n)) for n in dims]
+
+
+def _uniform_no_L(alpha, dims):
+    _, c = O.line_length(dims)
+    g = 0
+    for cd, ad in zip(c, alpha):
+        g = math.gcd(g, cd * int(ad))
+    return g == 1
+
+
+def _adjoint_forward_dft(g, alpha, tau, dims):
+    pts = O.line_points(dims, alpha, tau)
+    back = np.fft.fft(g, axis=-1) / g.shape[-1]
+    out = np.zeros(tuple(dims), np.complex128)
+    np.add.at(out, tuple(pts[..., d].reshape(-1) for d in range(len(dims))), back.reshape(-1))
+    return out
+
+
+def _classify_inverted_ratio(bins, alpha, tau, dims, p):
+    # decode from s_0 / s_{d+1} instead of s_{d+1} / s_0: the phase (and so k_d) changes sign
+    flipped = bins.copy()
+    with np.errstate(divide="ignore", invalid="ignore"):
+        flipped[1:] = np.nan_to_num(bins[0] * np.conj(bins[1:] / bins[0]))
+    return _orig["classify_decode"](flipped, alpha, tau, dims, p)
+
+
+def _synth_line0_only(k, a, alpha, tau, dims):
+    out = _orig["synth"](k, a, alpha, tau, dims)
+    out[1:] = out[:1]
+    return out
+
+
+MUTATIONS = {
+    "dft sign flipped": ("line_dft", _dft_plus_sign),
+    "dft 1/L dropped": ("line_dft", _dft_no_scale),
+    "offset lines not shifted": ("line_points", _points_no_shift),
+    "offset shifted on the wrong dimension": ("line_points", _points_shift_wrong_dim),
+    "slope components transposed in the bin map": ("bin_index", _bin_reversed_alpha),
+    "offset phase dropped": ("line_phase", _phase_no_tau),
+    "offset phase conjugated": ("line_phase", _phase_conj),
+    "line length is the product": ("line_length", _length_product),
+    "line length is the max": ("line_length", _length_max),
+    "uniformity test ignores L": ("uniform_projection", _uniform_no_L),
+    "adjoint uses the forward DFT": ("project_adjoint", _adjoint_forward_dft),
+    "decode uses the inverted ratio": ("classify_decode", _classify_inverted_ratio),
+    "synthesis ignores the offset lines": ("synth", _synth_line0_only),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, monkeypatch):
+    attr, fn = MUTATIONS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = []
+    for check in CHECKS:
+        try:
+            check(O)
+        except (AssertionError, ValueError, IndexError):
+            caught.append(check.__name__)
+    assert caught, f"no pin caught the planted mistake: {name}"
