@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Throughput of the batched FPS-SFT recovery loop on GB300.
+
+Workload (default): the uneven 2-D batch -- 4096 noiseless signals with shapes drawn uniformly
+from {64x64, 128x128, 128x256, 256x256}, K = ceil(N/200) unit-magnitude sinusoids each, line
+budget T = N / (3L) per signal, early stop.  One step = one fpssft_recover launch (captured in a
+CUDA graph) over the whole batch with inputs resident in HBM; between timed steps a 256 MiB buffer
+is written to flush L2.  The line prints signals/s, the roofline of the recovery kernel, the
+end-to-end rate through fpssft_recover_host (host buffers, copies included), the unfused
+per-signal GPU form on a sample, and the FP64 oracle on host cores on a bounded sample.
+
+Multi-GPU (torchrun): every rank recovers its own batch of the same recipe (independent seeds);
+there is no collective on the data path (weak scaling); a barrier and a max-reduce of the timed
+region are the only communication.
+
+--impl reference times the FP64 oracle (the reference implementation of this method) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "signals/s batched FPS-SFT vs plain per-signal GPU at exact support; HBM GB/s"
+UNIT = "signals/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fpssft", choices=["fpssft", "reference"])
+    ap.add_argument("--workload", default="uneven_2d")
+    ap.add_argument("--batch", type=int, default=None, help="override the signal count (smaller captures)")
+    ap.add_argument("--plain-sample", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--quick", action="store_true", help="only the timed device loop (for profiler runs)")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def stratified(wl, n, seed=0):
+    """n signal indices spread evenly over the distinct shapes of the workload."""
+    rng = np.random.default_rng(seed)
+    keys = [tuple(int(v) for v in d) for d in wl.dims]
+    groups = {}
+    for i, k in enumerate(keys):
+        groups.setdefault(k, []).append(i)
+    out = []
+    per = max(1, n // len(groups))
+    for k in sorted(groups):
+        g = groups[k]
+        out.extend(int(i) for i in rng.choice(g, min(per, len(g)), replace=False))
+    return out[:max(n, len(groups))]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in ("paper_1711_11407_gb300/csrc/fpssft.cu", "paper_1711_11407_gb300/csrc/fpssft_device.cuh"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, batch):
+    """DRAM bytes per launch of the recovery kernel from the committed ncu summary, when it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"k_recover_{workload}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None, None
+    if d.get("source_hash") != source_hash():
+        return None, path
+    per_signal = d["dram_bytes_per_launch"] / d["batch"]
+    return per_signal * batch, path
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for r in csv.reader(io.StringIO(getattr(self, "out", ""))):
+            r = [c.strip() for c in r]
+            if len(r) < 10:
+                continue
+            if self.uuid and self.uuid not in r[1]:
+                continue
+            rows.append(r)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(wl, params, seconds, order):
+    """FP64 oracle on the host: signals/s over a bounded sample (signals taken in `order`)."""
+    from oracle import fpssft_oracle as O
+    t0 = time.perf_counter()
+    n = 0
+    for b in order:
+        T = int(wl.T[b]) if params.T == 0 else params.T
+        O.recover(wl.cube(b), wl.alpha[b, :T], wl.tau[b, :T],
+                  O.Params(T=T, k_cap=params.k_cap, theta0=params.theta0, rho=params.rho, eta=params.eta,
+                           early_stop=params.early_stop))
+        n += 1
+        if time.perf_counter() - t0 >= seconds and n >= 4:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on host cores, each step a bounded sample of the workload."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_1711_11407_gb300 import configs, synth
+    wl = synth.make_workload(args.workload, batch=args.batch)
+    p = configs.params_for(wl)
+    per_step = 24
+    order = stratified(wl, per_step * (args.steps + args.warmup) + per_step, seed=1)
+    times = []
+    n_done = 0
+    for s in range(args.warmup + args.steps):
+        idx = order[(s * per_step) % len(order):][:per_step] or order[:per_step]
+        r, n, dt = oracle_rate(wl, p, 1e9, idx)
+        if s >= args.warmup:
+            times.append(dt)
+            n_done += n
+    total = sum(times)
+    value = n_done / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "batch": int(wl.batch), "signals_per_step": per_step,
+                       "note": "each step recovers a stratified sample of the workload's signals"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_done} signals over {args.steps} steps (stratified by shape)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from oracle import fpssft_oracle as O
+    from paper_1711_11407_gb300 import configs, synth
+    from paper_1711_11407_gb300.api import Plan
+
+    rank, local_rank, world = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    # ---- workload (each rank its own independent batch of the same recipe) ----------------------
+    seed = 1234 + 4 + 1000 * rank if args.workload == "uneven_2d" else None
+    if seed is None:
+        seed = 1234 + {v: k for k, v in synth.WORKLOAD_IDS.items()}[args.workload] + 1000 * rank
+    wl = synth.make_workload(args.workload, seed=seed, batch=args.batch)
+    p = configs.params_for(wl, threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+    plan = Plan(wl.dims, p)
+    cubes = torch.from_numpy(wl.cubes).to(dev)
+    offs = torch.from_numpy(wl.offsets).to(dev)
+    alpha = torch.from_numpy(wl.alpha).to(dev)
+    tau = torch.from_numpy(wl.tau).to(dev)
+    out = plan.alloc_output(dev)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        plan.recover(cubes, offs, alpha, tau, out=out)
+
+    with torch.cuda.stream(stream):
+        step()                       # first call outside capture (validates and warms the module)
+        stream.synchronize()
+        graph = None
+        if not args.no_graph:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+        run = graph.replay if graph is not None else step
+        for _ in range(max(3, args.warmup)):
+            run()
+        stream.synchronize()
+
+        # ---- timed device loop ---------------------------------------------------------------
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(uuid) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                run()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = wl.batch * world / (ms_per_step / 1000.0)
+
+    # ---- correctness of what was timed: exact support vs the planted spectra ---------------------
+    torch.cuda.synchronize()
+    ks, cnt, iters = out.k.cpu().numpy(), out.count.cpu().numpy(), out.iters.cpu().numpy()
+    ok = 0
+    for b in range(wl.batch):
+        dims = tuple(int(v) for v in wl.dims[b])
+        truth = np.sort(O.linear_index(wl.k_true[b], dims))
+        ok += int(np.array_equal(O.linear_index(ks[b, :cnt[b]].astype(np.int64), dims), truth))
+    success = ok / wl.batch
+
+    # ---- roofline of the recovery kernel ---------------------------------------------------------
+    L = plan.L.astype(np.int64)
+    useful = float(np.sum(iters.astype(np.int64) * (wl.D + 1) * L * 8))           # gathered sample bytes
+    peaks, peak_src = measured_peaks()
+    achieved = useful / (ms_per_step / 1000.0) / 1e9
+    traffic, _ = profiled_traffic(args.workload, wl.batch)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": traffic,
+                "peak_source": f"{peak_src} (hbm_gbs, copy bandwidth)",
+                "algorithmic_bytes_per_launch": useful,
+                "kernel": "k_recover<2> (persistent; one CTA per signal; timed per launch with CUDA events)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "batch_per_gpu": int(wl.batch), "global_batch": int(wl.batch * world),
+                       "shapes": sorted({"x".join(str(int(v)) for v in d) for d in wl.dims}),
+                       "K": "ceil(N/200)" if args.workload == "uneven_2d" else "per workload",
+                       "T": "N/(3L) per signal, early stop", "l2": "256 MiB written between timed steps",
+                       "cuda_graph": graph is not None, "parallelism": f"batch sharded over {world} GPU(s), no collective",
+                       "threads": plan.info["threads"], "grid": plan.info["grid"], "smem_bytes": plan.info["smem_bytes"]},
+            "roofline": roofline, "gpu_launches": args.steps, "exact_support_success": success,
+            "mean_iterations": float(np.mean(iters)), "clocks": clk.summary()}
+
+    if not args.quick:
+        # ---- end to end through the host-buffer call ------------------------------------------
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_cubes, h_offs, h_alpha, h_tau = pin(wl.cubes), pin(wl.offsets), pin(wl.alpha), pin(wl.tau)
+        h_out = plan.alloc_output("cpu")
+        for f in ("k", "a", "count", "iters", "status"):
+            setattr(h_out, f, getattr(h_out, f).pin_memory())
+        with torch.cuda.stream(stream):
+            plan.recover_host(h_cubes, h_offs, h_alpha, h_tau, out=h_out, stream=stream)
+            if world > 1:
+                dist.barrier()
+            e2e_ms = []
+            for _ in range(args.steps):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                plan.recover_host(h_cubes, h_offs, h_alpha, h_tau, out=h_out, stream=stream)
+                a1.record(stream)
+                a1.synchronize()
+                e2e_ms.append(a0.elapsed_time(a1))
+        te = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_step = float(te.item()) / args.steps
+        same = bool(torch.equal(h_out.count, out.count.cpu()))
+        h2d = sum(int(x.numel() * x.element_size()) for x in (h_cubes, h_offs, h_alpha, h_tau))
+        d2h = sum(int(getattr(h_out, f).numel() * getattr(h_out, f).element_size()) for f in ("k", "a", "count", "iters", "status"))
+        line["e2e"] = {"value": wl.batch * world / (e2e_step / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step, "call": "fpssft_recover_host",
+                       "matches_device_run": same}
+
+        # ---- plain per-signal GPU form on a sample ---------------------------------------------
+        from paper_1711_11407_gb300.plain import PlainRecoverer
+        sample = stratified(wl, args.plain_sample, seed=2)
+        pr = PlainRecoverer(p, dev)
+        pr.recover(wl, cubes, alpha, tau, sample[:4])       # warm-up (plans, cuFFT)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = pr.recover(wl, cubes, alpha, tau, sample)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        agree = all(np.array_equal(k, ks[b, :cnt[b]]) for (k, _, _, _), b in zip(res, sample))
+        plain_rate = len(sample) / dt
+        line["plain_gpu"] = {"value": plain_rate, "unit": UNIT, "sample": f"{len(sample)} signals stratified by shape",
+                             "same_support_as_batched": agree, "batched_over_plain": value / world / plain_rate}
+
+        # ---- FP64 oracle on the host cores (rank 0) --------------------------------------------
+        if rank == 0:
+            order = stratified(wl, 256, seed=3)
+            rate, n, dt = oracle_rate(wl, p, args.cpu_seconds, order)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{n} signals stratified by shape, {dt:.1f} s single-threaded numpy FP64",
+                                    "host_cores_available": len(os.sched_getaffinity(0))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

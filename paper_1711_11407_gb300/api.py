@@ -1,0 +1,216 @@
+"""PyTorch-facing wrapper of the FPS-SFT C ABI: device memory and streams come from torch, every
+computation happens in the CUDA library (see include/fpssft.h for the exact semantics)."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+__all__ = ["Params", "Plan", "RecoverOutput"]
+
+
+@dataclass
+class Params:
+    """Recovery parameters (fpssft_params).  T = 0 selects the per-signal budget N / ((D+1) L)."""
+
+    T: int = 10
+    k_cap: int = 1024
+    theta0: float = 1e-3
+    rho: float = 1e-3
+    eta: float = 0.05
+    early_stop: bool = True
+    peel_mode: int = 0
+    threads: int = 0
+    ctas_per_sm: int = 0
+
+    def c(self):
+        return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
+                            int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm))
+
+
+@dataclass
+class RecoverOutput:
+    k: torch.Tensor        # int32 [batch][k_cap][D]
+    a: torch.Tensor        # complex64 [batch][k_cap]
+    count: torch.Tensor    # int32 [batch]
+    iters: torch.Tensor    # int32 [batch]
+    status: torch.Tensor   # int32 [batch]
+
+    def signal(self, b):
+        """(k [n][D] int64 numpy, a [n] complex128 numpy) of signal b (synchronises)."""
+        n = int(self.count[b])
+        return (self.k[b, :n].cpu().numpy().astype(np.int64), self.a[b, :n].cpu().numpy().astype(np.complex128))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, name, device=True):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Plan:
+    """A plan for a batch of cubes with shapes dims[b] (array-like int [batch][D])."""
+
+    def __init__(self, dims, params: Params | None = None):
+        self.lib = _lib.load()
+        dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+        if dims.ndim != 2:
+            raise ValueError("dims must be [batch][D]")
+        self.dims = dims
+        self.params = params or Params()
+        self.batch, self.D = int(dims.shape[0]), int(dims.shape[1])
+        h = ctypes.c_void_p()
+        cp = self.params.c()
+        _lib.check(self.lib.fpssft_plan_create(ctypes.byref(h), self.D, self.batch,
+                                               dims.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cp)))
+        self.handle = h
+        info = _lib.PlanInfo()
+        _lib.check(self.lib.fpssft_plan_get_info(self.handle, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _lib.PlanInfo._fields_}
+        self.L_max, self.T_max, self.k_cap = info.L_max, info.T_max, info.k_cap
+        Ls = np.zeros(max(1, self.batch), np.int32)
+        Ts = np.zeros(max(1, self.batch), np.int32)
+        _lib.check(self.lib.fpssft_plan_get_lengths(self.handle, Ls.ctypes.data_as(ctypes.c_void_p),
+                                                    Ts.ctypes.data_as(ctypes.c_void_p)))
+        self.L = Ls[: self.batch]
+        self.T = Ts[: self.batch]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fpssft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- checks ----------------------------------------------------------------------------------
+    def _sched(self, alpha, tau, rows=None):
+        _need(alpha, torch.int32, "alpha")
+        _need(tau, torch.int32, "tau")
+        if alpha.shape != tau.shape or alpha.dim() != 3 or alpha.shape[0] != self.batch or alpha.shape[2] != self.D:
+            raise ValueError(f"alpha/tau must be int32 [batch={self.batch}][n_sched][D={self.D}]")
+        if rows is not None and alpha.shape[1] != rows:
+            raise ValueError(f"schedule must have {rows} rows per signal")
+        return alpha.shape[1]
+
+    def _bins_shape(self, n_sched):
+        return (self.batch, n_sched, self.D + 1, self.L_max)
+
+    # ---- calls -----------------------------------------------------------------------------------
+    def project(self, cubes, offsets, alpha, tau, out=None, stream=None, raw_lines=False):
+        """Line DFTs (or raw line samples) [batch][n_sched][D+1][L_max] complex64."""
+        _need(cubes, torch.complex64, "cubes")
+        _need(offsets, torch.int64, "offsets")
+        S = self._sched(alpha, tau)
+        if out is None:
+            out = torch.empty(self._bins_shape(S), dtype=torch.complex64, device=cubes.device)
+        _need(out, torch.complex64, "out")
+        fn = self.lib.fpssft_lines if raw_lines else self.lib.fpssft_project
+        _lib.check(fn(self.handle, _ptr(cubes), _ptr(offsets), _ptr(alpha), _ptr(tau), S, _ptr(out), _stream(stream)))
+        return out
+
+    def lines(self, cubes, offsets, alpha, tau, out=None, stream=None):
+        return self.project(cubes, offsets, alpha, tau, out, stream, raw_lines=True)
+
+    def alloc_output(self, device="cuda"):
+        return RecoverOutput(torch.zeros((self.batch, self.k_cap, self.D), dtype=torch.int32, device=device),
+                             torch.zeros((self.batch, self.k_cap), dtype=torch.complex64, device=device),
+                             torch.zeros(self.batch, dtype=torch.int32, device=device),
+                             torch.zeros(self.batch, dtype=torch.int32, device=device),
+                             torch.zeros(self.batch, dtype=torch.int32, device=device))
+
+    def recover(self, cubes, offsets, alpha, tau, out: RecoverOutput | None = None, init_count=None, stream=None):
+        """The fused persistent recovery over the batch; schedule [batch][T_max][D]."""
+        _need(cubes, torch.complex64, "cubes")
+        _need(offsets, torch.int64, "offsets")
+        self._sched(alpha, tau, rows=self.T_max)
+        if out is None:
+            out = self.alloc_output(cubes.device)
+        if init_count is not None:
+            _need(init_count, torch.int32, "init_count")
+        _lib.check(self.lib.fpssft_recover(self.handle, _ptr(cubes), _ptr(offsets), _ptr(alpha), _ptr(tau),
+                                           _ptr(init_count), _ptr(out.k), _ptr(out.a), _ptr(out.count),
+                                           _ptr(out.iters), _ptr(out.status), _stream(stream)))
+        return out
+
+    def recover_host(self, cubes, offsets, alpha, tau, out=None, init_count=None, stream=None):
+        """fpssft_recover_host on host arrays (numpy or pinned CPU tensors); returns host outputs."""
+        def host(t, dtype):
+            if isinstance(t, torch.Tensor):
+                if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+                    raise ValueError("host tensors must be contiguous CPU tensors of the right dtype")
+                return t
+            return torch.from_numpy(np.ascontiguousarray(t)).to(dtype)
+        cubes = host(cubes, torch.complex64)
+        offsets = host(offsets, torch.int64)
+        alpha = host(alpha, torch.int32)
+        tau = host(tau, torch.int32)
+        if out is None:
+            out = self.alloc_output("cpu")
+        _lib.check(self.lib.fpssft_recover_host(self.handle, _ptr(cubes), _ptr(offsets), _ptr(alpha), _ptr(tau),
+                                                _ptr(init_count), _ptr(out.k), _ptr(out.a), _ptr(out.count),
+                                                _ptr(out.iters), _ptr(out.status), _stream(stream)))
+        return out
+
+    def synth(self, alpha, tau, k, a, count, accumulate=0, bins=None, stream=None):
+        """Bins of the sparse spectrum (k, a) on the schedule lines (accumulate: 0 set, +1 add, -1 subtract)."""
+        S = self._sched(alpha, tau)
+        _need(k, torch.int32, "k")
+        _need(a, torch.complex64, "a")
+        _need(count, torch.int32, "count")
+        if bins is None:
+            bins = torch.empty(self._bins_shape(S), dtype=torch.complex64, device=a.device)
+            accumulate = 0
+        _need(bins, torch.complex64, "bins")
+        _lib.check(self.lib.fpssft_synth(self.handle, _ptr(alpha), _ptr(tau), S, _ptr(k), _ptr(a), _ptr(count),
+                                         int(accumulate), _ptr(bins), _stream(stream)))
+        return bins
+
+    def decode(self, bins, alpha, tau, k, a, count, t0_count, status, stream=None):
+        self._sched(alpha, tau, rows=1)
+        _lib.check(self.lib.fpssft_decode(self.handle, _ptr(bins), _ptr(alpha), _ptr(tau), _ptr(k), _ptr(a),
+                                          _ptr(count), _ptr(t0_count), _ptr(status), _stream(stream)))
+
+    def finalize(self, k, a, count, stream=None):
+        _lib.check(self.lib.fpssft_finalize(self.handle, _ptr(k), _ptr(a), _ptr(count), _stream(stream)))
+
+    def adjoint_project(self, grad_bins, offsets, alpha, tau, grad_cubes, stream=None):
+        """grad_cubes += P^H grad_bins (cube layout at offsets)."""
+        S = self._sched(alpha, tau)
+        _need(grad_bins, torch.complex64, "grad_bins")
+        _need(grad_cubes, torch.complex64, "grad_cubes")
+        _lib.check(self.lib.fpssft_adjoint(self.handle, _lib.ADJ_PROJECT, _ptr(grad_bins), _ptr(offsets),
+                                           _ptr(alpha), _ptr(tau), S, None, None, _ptr(grad_cubes), _stream(stream)))
+        return grad_cubes
+
+    def adjoint_synth(self, grad_bins, alpha, tau, k, count, grad_a=None, stream=None):
+        """grad_a = S^H grad_bins for the set (k, count); entries i >= count[b] are left untouched."""
+        S = self._sched(alpha, tau)
+        _need(grad_bins, torch.complex64, "grad_bins")
+        if grad_a is None:
+            grad_a = torch.zeros((self.batch, self.k_cap), dtype=torch.complex64, device=grad_bins.device)
+        _lib.check(self.lib.fpssft_adjoint(self.handle, _lib.ADJ_SYNTH, _ptr(grad_bins), None, _ptr(alpha),
+                                           _ptr(tau), S, _ptr(k), _ptr(count), _ptr(grad_a), _stream(stream)))
+        return grad_a

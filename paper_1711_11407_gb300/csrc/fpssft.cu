@@ -1,0 +1,1194 @@
+// FPS-SFT recovery loop for GB300 (sm_103a): kernels and the C ABI declared in include/fpssft.h.
+//
+// Paper: Wang, Patel, Petropulu, "FPS-SFT: A Multi-dimensional Sparse Fourier Transform Based on
+// the Fourier Projection-slice Theorem", arXiv 1711.11407.  The iteration of Sec. 2.2 (sample the
+// D+1 lines, L-point DFT, subtract the recovered set, decode 1-sparse bins, merge) runs inside one
+// persistent kernel: each CTA pulls a signal from a longest-first queue and keeps its lines, bins,
+// twiddles and recovered set in shared memory for all of that signal's iterations, so the only
+// global traffic per iteration is the (D+1) L sample gather.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "fpssft.h"
+#include "fpssft_device.cuh"
+
+using namespace fpssft;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fpssft_status fail(fpssft_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define FPSSFT_CUDA_TRY(call)                                                                    \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      return fail(FPSSFT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                            \
+  } while (0)
+
+constexpr int kStatusCapacity = FPSSFT_ERR_CAPACITY;
+
+// The dynamic shared-memory limit is a property of the kernel (per device), shared by every plan:
+// raise it when a plan needs more, never lower it under a plan that needs more.
+std::mutex g_attr_mutex;
+std::map<std::pair<int, const void*>, int> g_attr_bytes;
+
+cudaError_t ensure_dynamic_smem(const void* func, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  int& cur = g_attr_bytes[{dev, func}];
+  if ((int)bytes <= cur) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = (int)bytes;
+  return e;
+}
+
+struct DeviceTables {
+  const Shape* shapes;
+  const int* sig_shape;
+  const int* sig_T;
+  const int* order;
+  const float2* twiddles;
+};
+
+}  // namespace
+
+// ================================================================================================
+// Kernels
+// ================================================================================================
+
+struct RecoverArgs {
+  const float2* cubes;
+  const int64_t* offsets;
+  const int* alpha;
+  const int* tau;
+  int sched_stride;          // T_max * D
+  DeviceTables tab;
+  int* work_counter;
+  int batch;
+  int k_cap;
+  int hash_bits;
+  int L_max;
+  int tw_smem;
+  int early_stop;
+  Thresholds th;
+  const int* init_count;
+  int* out_k;
+  float2* out_a;
+  int* out_count;
+  int* out_iters;
+  int* out_status;
+};
+
+struct SmemLayout {
+  size_t bufA, bufB, tw, la, lk, lkey, hkey, hidx, total;
+};
+
+static __host__ __device__ SmemLayout recover_layout(int D, int L_max, int k_cap, int hash_cap, bool tw_smem) {
+  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
+  SmemLayout s{};
+  size_t off = 0;
+  const size_t lines = (size_t)(D + 1) * L_max * sizeof(float2);
+  s.bufA = off; off = al(off + lines);
+  s.bufB = off; off = al(off + lines);
+  s.tw = off; off = al(off + (tw_smem ? (size_t)L_max * sizeof(float2) : 0));
+  s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
+  s.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
+  s.lkey = off; off = al(off + (size_t)k_cap * sizeof(int));
+  s.hkey = off; off = al(off + (size_t)hash_cap * sizeof(int));
+  s.hidx = off; off = al(off + (size_t)hash_cap * sizeof(int));
+  s.total = off;
+  return s;
+}
+
+// Copy a Shape into shared memory (cooperatively) and, when twiddles live in shared memory, its
+// twiddle table.  Caller synchronises afterwards.
+__device__ __forceinline__ void load_shape(Shape& sh, const Shape* __restrict__ shapes, int si, float2* tws,
+                                           const float2* __restrict__ twiddles, bool tw_smem) {
+  const int* src = reinterpret_cast<const int*>(shapes + si);
+  int* dst = reinterpret_cast<int*>(&sh);
+  for (int i = threadIdx.x; i < (int)(sizeof(Shape) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  if (tw_smem) {
+    const int L = shapes[si].L;
+    const float2* t = twiddles + shapes[si].tw_off;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = t[i];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
+  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+
+  const SmemLayout lay = recover_layout(D, A.L_max, A.k_cap, 1 << A.hash_bits, A.tw_smem != 0);
+  float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
+  float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
+  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  SetView set;
+  set.la = reinterpret_cast<float2*>(smem + lay.la);
+  set.lk = reinterpret_cast<int*>(smem + lay.lk);
+  set.lkey = reinterpret_cast<int*>(smem + lay.lkey);
+  set.hkey = reinterpret_cast<int*>(smem + lay.hkey);
+  set.hidx = reinterpret_cast<int*>(smem + lay.hidx);
+  set.count = &s_count;
+  set.k_cap = A.k_cap;
+  set.hash_bits = A.hash_bits;
+  const int hash_cap = 1 << A.hash_bits;
+
+  int loaded = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
+    __syncthreads();
+    const int qi = s_sig;
+    if (qi >= A.batch) break;
+    const int b = A.tab.order[qi];
+    const int si = A.tab.sig_shape[b];
+    if (si != loaded) {
+      load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, A.tw_smem != 0);
+      loaded = si;
+    }
+    for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) set.hkey[i] = kEmpty;
+    if (threadIdx.x == 0) {
+      s_count = 0;
+      s_ovf = 0;
+    }
+    __syncthreads();
+    const float2* tw = A.tw_smem ? tws : A.tab.twiddles + sh.tw_off;
+    const int L = sh.L;
+    const float2* x = A.cubes + A.offsets[b];
+    int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
+    float2* oa_out = A.out_a + (size_t)b * A.k_cap;
+
+    if (A.init_count != nullptr) {   // resume from a given set
+      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
+      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        int k[D];
+        int key = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          k[d] = ok_out[i * D + d];
+          key += k[d] * sh.strides[d];
+        }
+        if (on_grid<D>(sh, k) && !set_insert<D>(set, k, key, oa_out[i])) atomicOr(&s_ovf, 1);
+      }
+      __syncthreads();
+    }
+
+    const int T = A.tab.sig_T[b];
+    int iters = 0;
+    for (int t = 0; t < T; ++t) {
+      const int* al = A.alpha + (size_t)b * A.sched_stride + t * D;
+      const int* ta = A.tau + (size_t)b * A.sched_stride + t * D;
+      if (threadIdx.x < D) {
+        const int d = threadIdx.x;
+        s_ca[d] = cmod(sh.c[d], al[d], L);
+        s_ct[d] = cmod(sh.c[d], ta[d], L);
+      }
+      gather_lines<D>(bufA, x, sh, al, ta);
+      __syncthreads();
+      if (threadIdx.x == 0) s_t0 = 0;
+      float2* bins = fft_lines(bufA, bufB, D + 1, sh, tw, 1.0f / (float)L);
+      peel_set<D>(bins, sh, set, min(s_count, A.k_cap), s_ca, s_ct, tw);
+      __syncthreads();
+      decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf);
+      __syncthreads();
+      iters = t + 1;
+      const bool stop = (A.early_stop && s_t0 == 0) || s_ovf != 0;
+      if (stop) break;
+    }
+
+    // output: keep |a| > theta0, sorted by linear index (hash arrays reused as sort buffers)
+    const int count = min(s_count, A.k_cap);
+    sort_kept(set, count, A.th.th0sq, set.hkey, set.hidx, &s_n);
+    const int n = s_n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int i = set.hidx[r];
+#pragma unroll
+      for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
+      oa_out[r] = set.la[i];
+    }
+    if (threadIdx.x == 0) {
+      A.out_count[b] = n;
+      A.out_iters[b] = iters;
+      A.out_status[b] = s_ovf ? kStatusCapacity : 0;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- projection / raw lines: one CTA per (signal, schedule row) --------------------------------
+struct ProjectArgs {
+  const float2* cubes;
+  const int64_t* offsets;
+  const int* alpha;
+  const int* tau;
+  int n_sched;
+  DeviceTables tab;
+  int batch;
+  int L_max;
+  int dft;
+  float2* out;      // [batch][n_sched][D+1][L_max]
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_project(ProjectArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  float2* bufA = reinterpret_cast<float2*>(smem);
+  float2* bufB = bufA + (size_t)(D + 1) * A.L_max;
+  int loaded = -1;
+  const long long units = (long long)A.batch * A.n_sched;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int b = (int)(u / A.n_sched);
+    const int si = A.tab.sig_shape[b];
+    if (si != loaded) {
+      __syncthreads();
+      load_shape(sh, A.tab.shapes, si, nullptr, A.tab.twiddles, false);
+      loaded = si;
+      __syncthreads();
+    }
+    const int L = sh.L;
+    const int* al = A.alpha + u * D;
+    const int* ta = A.tau + u * D;
+    gather_lines<D>(bufA, A.cubes + A.offsets[b], sh, al, ta);
+    __syncthreads();
+    const float2* res = A.dft ? fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L) : bufA;
+    float2* o = A.out + u * (D + 1) * (long long)A.L_max;
+    for (int i = threadIdx.x; i < (D + 1) * A.L_max; i += blockDim.x) {
+      const int j = i / A.L_max, m = i - j * A.L_max;
+      o[i] = (m < L) ? res[j * L + m] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- synthesis (+, overwrite / accumulate) and peel (-) ------------------------------------------
+struct SynthArgs {
+  const int* alpha;
+  const int* tau;
+  int n_sched;
+  DeviceTables tab;
+  int batch;
+  int L_max;
+  int k_cap;
+  const int* k;
+  const float2* a;
+  const int* count;
+  int accumulate;   // 0 overwrite, +1 add, -1 subtract
+  float2* bins;
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_synth(SynthArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+  float2* acc = reinterpret_cast<float2*>(smem);
+  int loaded = -1;
+  const long long units = (long long)A.batch * A.n_sched;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int b = (int)(u / A.n_sched);
+    const int si = A.tab.sig_shape[b];
+    __syncthreads();
+    if (si != loaded) {
+      load_shape(sh, A.tab.shapes, si, nullptr, A.tab.twiddles, false);
+      loaded = si;
+      __syncthreads();
+    }
+    const int L = sh.L;
+    const int* al = A.alpha + u * D;
+    const int* ta = A.tau + u * D;
+    if (threadIdx.x < D) {
+      const int d = threadIdx.x;
+      s_ca[d] = cmod(sh.c[d], al[d], L);
+      s_ct[d] = cmod(sh.c[d], ta[d], L);
+    }
+    float2* o = A.bins + u * (D + 1) * (long long)A.L_max;
+    for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
+      const int j = i / L, m = i - j * L;
+      acc[i] = A.accumulate ? o[j * A.L_max + m] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float sign = A.accumulate < 0 ? -1.f : 1.f;
+    const int cnt = min(max(A.count[b], 0), A.k_cap);
+    const float2* tw = A.tab.twiddles + sh.tw_off;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      int k[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) k[d] = A.k[((size_t)b * A.k_cap + i) * D + d];
+      if (on_grid<D>(sh, k)) project_entry<D>(acc, L, sh, k, A.a[(size_t)b * A.k_cap + i], s_ca, s_ct, tw, sign);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (D + 1) * A.L_max; i += blockDim.x) {
+      const int j = i / A.L_max, m = i - j * A.L_max;
+      o[i] = (m < L) ? acc[j * L + m] : make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// ---- one iteration's decode + merge on bins in global memory (unfused form) ----------------------
+struct DecodeArgs {
+  const float2* bins;   // [batch][1][D+1][L_max]
+  const int* alpha;
+  const int* tau;
+  DeviceTables tab;
+  int batch;
+  int L_max;
+  int k_cap;
+  int hash_bits;
+  Thresholds th;
+  int* k;
+  float2* a;
+  int* count;
+  int* t0_count;
+  int* status;
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_count, s_t0, s_ovf;
+  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+  const int hash_cap = 1 << A.hash_bits;
+  SetView set;
+  set.la = reinterpret_cast<float2*>(smem);
+  set.lk = reinterpret_cast<int*>(set.la + A.k_cap);
+  set.lkey = set.lk + (size_t)D * A.k_cap;
+  set.hkey = set.lkey + A.k_cap;
+  set.hidx = set.hkey + hash_cap;
+  set.count = &s_count;
+  set.k_cap = A.k_cap;
+  set.hash_bits = A.hash_bits;
+  for (int b = blockIdx.x; b < A.batch; b += gridDim.x) {
+    __syncthreads();
+    load_shape(sh, A.tab.shapes, A.tab.sig_shape[b], nullptr, A.tab.twiddles, false);
+    for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) set.hkey[i] = kEmpty;
+    if (threadIdx.x == 0) {
+      s_count = 0;
+      s_t0 = 0;
+      s_ovf = 0;
+    }
+    __syncthreads();
+    const int L = sh.L;
+    if (threadIdx.x < D) {
+      const int d = threadIdx.x;
+      s_ca[d] = cmod(sh.c[d], A.alpha[b * D + d], L);
+      s_ct[d] = cmod(sh.c[d], A.tau[b * D + d], L);
+    }
+    const int n0 = min(max(A.count[b], 0), A.k_cap);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      int k[D];
+      int key = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        k[d] = A.k[((size_t)b * A.k_cap + i) * D + d];
+        key += k[d] * sh.strides[d];
+      }
+      if (on_grid<D>(sh, k)) set_insert<D>(set, k, key, A.a[(size_t)b * A.k_cap + i]);
+    }
+    __syncthreads();
+    decode_bins<D>(A.bins + (size_t)b * (D + 1) * A.L_max, A.L_max, sh, set, s_ca, s_ct,
+                   A.tab.twiddles + sh.tw_off, A.th, &s_t0, &s_ovf);
+    __syncthreads();
+    const int cnt = min(s_count, A.k_cap);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) A.k[((size_t)b * A.k_cap + i) * D + d] = set.lk[d * A.k_cap + i];
+      A.a[(size_t)b * A.k_cap + i] = set.la[i];
+    }
+    if (threadIdx.x == 0) {
+      A.count[b] = cnt;
+      A.t0_count[b] = s_t0;
+      if (s_ovf) A.status[b] |= kStatusCapacity;
+    }
+  }
+}
+
+// ---- finalize: drop small amplitudes and sort (unfused form) -------------------------------------
+struct FinalizeArgs {
+  DeviceTables tab;
+  int batch;
+  int k_cap;
+  int sort_cap;     // power of two >= k_cap
+  double th0sq;
+  int* k;
+  float2* a;
+  int* count;
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_finalize(FinalizeArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_n;
+  SetView set;
+  set.la = reinterpret_cast<float2*>(smem);
+  set.lk = reinterpret_cast<int*>(set.la + A.k_cap);
+  set.lkey = set.lk + (size_t)D * A.k_cap;
+  int* skey = set.lkey + A.k_cap;
+  int* sidx = skey + A.sort_cap;
+  set.k_cap = A.k_cap;
+  for (int b = blockIdx.x; b < A.batch; b += gridDim.x) {
+    __syncthreads();
+    load_shape(sh, A.tab.shapes, A.tab.sig_shape[b], nullptr, A.tab.twiddles, false);
+    __syncthreads();
+    const int n0 = min(max(A.count[b], 0), A.k_cap);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      int key = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int kd = A.k[((size_t)b * A.k_cap + i) * D + d];
+        set.lk[d * A.k_cap + i] = kd;
+        key += kd * sh.strides[d];
+      }
+      set.lkey[i] = key;
+      set.la[i] = A.a[(size_t)b * A.k_cap + i];
+    }
+    __syncthreads();
+    sort_kept(set, n0, A.th0sq, skey, sidx, &s_n);
+    const int n = s_n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int i = sidx[r];
+#pragma unroll
+      for (int d = 0; d < D; ++d) A.k[((size_t)b * A.k_cap + r) * D + d] = set.lk[d * A.k_cap + i];
+      A.a[(size_t)b * A.k_cap + r] = set.la[i];
+    }
+    if (threadIdx.x == 0) A.count[b] = n;
+  }
+}
+
+// ---- adjoints --------------------------------------------------------------------------------
+struct AdjProjectArgs {
+  const float2* g;         // [batch][n_sched][D+1][L_max]
+  const int64_t* offsets;
+  const int* alpha;
+  const int* tau;
+  int n_sched;
+  DeviceTables tab;
+  int batch;
+  int L_max;
+  float2* grad;            // cube layout
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_adjoint_project(AdjProjectArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  float2* bufA = reinterpret_cast<float2*>(smem);
+  float2* bufB = bufA + (size_t)(D + 1) * A.L_max;
+  int loaded = -1;
+  const long long units = (long long)A.batch * A.n_sched;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int b = (int)(u / A.n_sched);
+    const int si = A.tab.sig_shape[b];
+    if (si != loaded) {
+      __syncthreads();
+      load_shape(sh, A.tab.shapes, si, nullptr, A.tab.twiddles, false);
+      loaded = si;
+      __syncthreads();
+    }
+    const int L = sh.L;
+    const float2* g = A.g + u * (D + 1) * (long long)A.L_max;
+    for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
+      const int j = i / L, m = i - j * L;
+      const float2 v = g[j * A.L_max + m];
+      bufA[i] = make_float2(v.x, -v.y);          // conj(g)
+    }
+    __syncthreads();
+    // (1/L) sum_m g(m) exp(+j 2 pi l m / L) = conj( (1/L) DFT(conj g) )
+    const float2* res = fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L);
+    int al[D], ta[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      al[d] = A.alpha[u * D + d];
+      ta[d] = A.tau[u * D + d];
+    }
+    float2* out = A.grad + A.offsets[b];
+    for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
+      const int j = i / L, l = i - j * L;
+      const float2 v = res[i];
+      const int addr = line_address<D>(sh, al, ta, j, l);
+      atomicAdd(&out[addr].x, v.x);
+      atomicAdd(&out[addr].y, -v.y);
+    }
+    __syncthreads();
+  }
+}
+
+struct AdjSynthArgs {
+  const float2* g;         // [batch][n_sched][D+1][L_max]
+  const int* alpha;
+  const int* tau;
+  int n_sched;
+  DeviceTables tab;
+  int batch;
+  int L_max;
+  int k_cap;
+  const int* k;
+  const int* count;
+  float2* grad_a;          // [batch][k_cap]
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_adjoint_synth(AdjSynthArgs A) {
+  const long long total = (long long)A.batch * A.k_cap;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / A.k_cap);
+    const int i = (int)(t - (long long)b * A.k_cap);
+    if (i >= min(max(A.count[b], 0), A.k_cap)) continue;
+    const Shape& sh = A.tab.shapes[A.tab.sig_shape[b]];
+    const int L = sh.L;
+    const float2* tw = A.tab.twiddles + sh.tw_off;
+    int k[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) k[d] = A.k[((size_t)b * A.k_cap + i) * D + d];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < A.n_sched && on_grid<D>(sh, k); ++s) {
+      const long long u = (long long)b * A.n_sched + s;
+      long long msum = 0, psum = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        msum += (long long)cmod(sh.c[d], A.alpha[u * D + d], L) * k[d];
+        psum += (long long)cmod(sh.c[d], A.tau[u * D + d], L) * k[d];
+      }
+      const int m = (int)(msum % L);
+      const int p = (int)(psum % L);
+      const float2* g = A.g + u * (D + 1) * (long long)A.L_max;
+      acc = cadd(acc, cmul(tw[p], g[m]));      // conj(W^p) = tw[p]
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        int q = p + sh.c[d] * k[d];
+        if (q >= L) q -= L;
+        acc = cadd(acc, cmul(tw[q], g[(d + 1) * A.L_max + m]));
+      }
+    }
+    A.grad_a[(size_t)b * A.k_cap + i] = acc;
+  }
+}
+
+// ================================================================================================
+// Host side: plan
+// ================================================================================================
+
+struct fpssft_plan_s {
+  int device = 0;
+  int D = 0;
+  int batch = 0;
+  fpssft_params p{};
+  int L_max = 1;
+  int T_max = 1;
+  int hash_bits = 1;
+  int n_shapes = 0;
+  int threads = 256;
+  int grid = 1;
+  int sm_count = 1;
+  bool tw_smem = true;
+  size_t smem = 0;
+  size_t total_elems = 0;   // sum of N_b (for host staging)
+  std::vector<Shape> shapes;
+  std::vector<int> sig_shape, sig_T, order, sig_L;
+  // device workspace
+  Shape* d_shapes = nullptr;
+  int* d_sig_shape = nullptr;
+  int* d_sig_T = nullptr;
+  int* d_order = nullptr;
+  float2* d_twiddles = nullptr;
+  int* d_counter = nullptr;
+  // host-call staging (allocated on the first fpssft_recover_host call)
+  void* st_cubes = nullptr;
+  size_t st_cubes_elems = 0;
+  int64_t* st_offsets = nullptr;
+  int32_t* st_alpha = nullptr;
+  int32_t* st_tau = nullptr;
+  int32_t* st_init = nullptr;
+  int32_t* st_k = nullptr;
+  void* st_a = nullptr;
+  int32_t* st_count = nullptr;
+  int32_t* st_iters = nullptr;
+  int32_t* st_status = nullptr;
+
+  DeviceTables tables() const { return DeviceTables{d_shapes, d_sig_shape, d_sig_T, d_order, d_twiddles}; }
+  Thresholds thresholds() const {
+    Thresholds t;
+    t.th0sq = (double)p.theta0 * (double)p.theta0;
+    t.rho = p.rho;
+    t.eta = p.eta;
+    return t;
+  }
+};
+
+namespace {
+
+std::vector<int> factorize(int L) {
+  std::vector<int> r;
+  int n = L;
+  while (n % 8 == 0) { r.push_back(8); n /= 8; }
+  while (n % 4 == 0) { r.push_back(4); n /= 4; }
+  while (n % 2 == 0) { r.push_back(2); n /= 2; }
+  while (n % 3 == 0) { r.push_back(3); n /= 3; }
+  while (n % 5 == 0) { r.push_back(5); n /= 5; }
+  for (int f = 7; (long long)f * f <= n; f += 2) {
+    while (n % f == 0) { r.push_back(f); n /= f; }
+  }
+  if (n > 1) r.push_back(n);
+  return r;
+}
+
+template <typename F>
+fpssft_status dispatch_D(int D, F&& f) {
+  switch (D) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    default: return fail(FPSSFT_ERR_INVALID, "D must be in [1, 4]");
+  }
+}
+
+void free_plan_memory(fpssft_plan_s* p) {
+  cudaFree(p->d_shapes);
+  cudaFree(p->d_sig_shape);
+  cudaFree(p->d_sig_T);
+  cudaFree(p->d_order);
+  cudaFree(p->d_twiddles);
+  cudaFree(p->d_counter);
+  cudaFree(p->st_cubes);
+  cudaFree(p->st_offsets);
+  cudaFree(p->st_alpha);
+  cudaFree(p->st_tau);
+  cudaFree(p->st_init);
+  cudaFree(p->st_k);
+  cudaFree(p->st_a);
+  cudaFree(p->st_count);
+  cudaFree(p->st_iters);
+  cudaFree(p->st_status);
+}
+
+size_t line_smem(int D, int L_max) { return 2 * (size_t)(D + 1) * L_max * sizeof(float2); }
+
+}  // namespace
+
+extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch, const int64_t* dims,
+                                            const fpssft_params* params) {
+  g_last_error.clear();
+  if (out == nullptr || params == nullptr) return fail(FPSSFT_ERR_INVALID, "null out or params");
+  *out = nullptr;
+  if (D < 1 || D > kMaxD) return fail(FPSSFT_ERR_INVALID, "D must be in [1, 4]");
+  if (batch < 0) return fail(FPSSFT_ERR_INVALID, "batch must be >= 0");
+  if (batch > 0 && dims == nullptr) return fail(FPSSFT_ERR_INVALID, "null dims");
+  const fpssft_params& pr = *params;
+  if (pr.k_cap < 1 || pr.k_cap > (1 << 22)) return fail(FPSSFT_ERR_INVALID, "k_cap must be in [1, 2^22]");
+  if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
+  if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
+  if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
+  if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
+
+  auto* P = new (std::nothrow) fpssft_plan_s();
+  if (!P) return fail(FPSSFT_ERR_ALLOC, "host allocation failed");
+  P->D = D;
+  P->batch = batch;
+  P->p = pr;
+  cudaGetDevice(&P->device);
+
+  std::map<std::vector<int>, int> shape_id;
+  std::map<int, int> tw_off;
+  std::vector<float2> tw_pool;
+  P->sig_shape.resize(batch);
+  P->sig_T.resize(batch);
+  P->sig_L.resize(batch);
+  size_t total = 0;
+  for (int b = 0; b < batch; ++b) {
+    std::vector<int> dv(D);
+    long long N = 1, L = 1, nmax = 1;
+    for (int d = 0; d < D; ++d) {
+      const int64_t n = dims[(size_t)b * D + d];
+      if (n < 1 || n > (1 << 24)) { delete P; return fail(FPSSFT_ERR_INVALID, "every dimension must be in [1, 2^24]"); }
+      dv[d] = (int)n;
+      N *= n;
+      L = L / std::gcd(L, (long long)n) * n;
+      nmax = std::max(nmax, (long long)n);
+      if (N > (1LL << 31) - 1 || L > (1LL << 24)) { delete P; return fail(FPSSFT_ERR_UNSUPPORTED, "cube or line too large (N < 2^31, L <= 2^24)"); }
+    }
+    if ((long long)D * L * nmax >= (1LL << 31)) { delete P; return fail(FPSSFT_ERR_UNSUPPORTED, "D * L * max N_d must stay below 2^31"); }
+    total += (size_t)N;
+    auto it = shape_id.find(dv);
+    int si;
+    if (it == shape_id.end()) {
+      Shape sh{};
+      sh.D = D;
+      sh.L = (int)L;
+      sh.N = (int)N;
+      int stride = 1;
+      for (int d = D - 1; d >= 0; --d) { sh.dims[d] = dv[d]; sh.strides[d] = stride; stride *= dv[d]; }
+      for (int d = 0; d < D; ++d) sh.c[d] = (int)(L / dv[d]);
+      auto rad = factorize((int)L);
+      if ((int)rad.size() > kMaxStages) { delete P; return fail(FPSSFT_ERR_UNSUPPORTED, "too many FFT stages"); }
+      sh.nst = (int)rad.size();
+      for (size_t s = 0; s < rad.size(); ++s) sh.radix[s] = rad[s];
+      auto t = tw_off.find((int)L);
+      if (t == tw_off.end()) {
+        const int off = (int)tw_pool.size();
+        tw_off[(int)L] = off;
+        for (long long q = 0; q < L; ++q) {
+          // exp(-j 2 pi q / L) in FP64, rounded to FP32
+          const double ang = 2.0 * M_PI * (double)q / (double)L;
+          tw_pool.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
+        }
+        sh.tw_off = off;
+      } else {
+        sh.tw_off = t->second;
+      }
+      si = (int)P->shapes.size();
+      shape_id[dv] = si;
+      P->shapes.push_back(sh);
+    } else {
+      si = it->second;
+    }
+    P->sig_shape[b] = si;
+    P->sig_L[b] = (int)L;
+    const long long budget = std::max(1LL, N / ((long long)(D + 1) * L));
+    P->sig_T[b] = pr.T > 0 ? pr.T : (int)std::min(budget, (long long)1 << 30);
+    P->L_max = std::max(P->L_max, (int)L);
+    P->T_max = std::max(P->T_max, P->sig_T[b]);
+  }
+  P->total_elems = total;
+  P->n_shapes = (int)P->shapes.size();
+  // longest lines first, then the larger iteration budget (longest-processing-time order)
+  P->order.resize(batch);
+  std::iota(P->order.begin(), P->order.end(), 0);
+  std::stable_sort(P->order.begin(), P->order.end(), [&](int a, int b) {
+    if (P->sig_L[a] != P->sig_L[b]) return P->sig_L[a] > P->sig_L[b];
+    return P->sig_T[a] > P->sig_T[b];
+  });
+  int hb = 1;
+  while ((1 << hb) < 2 * pr.k_cap) ++hb;
+  P->hash_bits = hb;
+
+  int dev = P->device;
+  int optin = 0, sms = 1;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (optin <= 0) optin = 227 * 1024;
+  if (sms <= 0) sms = 1;
+  P->sm_count = sms;
+  const size_t static_reserve = sizeof(Shape) + 256;
+  SmemLayout lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true);
+  P->tw_smem = true;
+  if (lay.total + static_reserve > (size_t)optin) {
+    lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false);
+    P->tw_smem = false;
+  }
+  if (lay.total + static_reserve > (size_t)optin) {
+    delete P;
+    return fail(FPSSFT_ERR_UNSUPPORTED, "lines + recovered set exceed one CTA's shared memory (L_max or k_cap too large)");
+  }
+  P->smem = lay.total;
+  if (pr.threads > 0) {
+    P->threads = pr.threads;
+  } else {
+    int t = 64;
+    while (t < P->L_max && t < 512) t <<= 1;
+    P->threads = t;
+  }
+
+  // device workspace
+  auto cleanup_fail = [&](const char* what, cudaError_t e) {
+    free_plan_memory(P);
+    delete P;
+    return fail(e == cudaErrorMemoryAllocation ? FPSSFT_ERR_ALLOC : FPSSFT_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  const size_t nb = std::max(1, batch);
+  if ((e = cudaMalloc(&P->d_shapes, std::max<size_t>(1, P->shapes.size()) * sizeof(Shape))) != cudaSuccess) return cleanup_fail("cudaMalloc shapes", e);
+  if ((e = cudaMalloc(&P->d_sig_shape, nb * sizeof(int))) != cudaSuccess) return cleanup_fail("cudaMalloc sig_shape", e);
+  if ((e = cudaMalloc(&P->d_sig_T, nb * sizeof(int))) != cudaSuccess) return cleanup_fail("cudaMalloc sig_T", e);
+  if ((e = cudaMalloc(&P->d_order, nb * sizeof(int))) != cudaSuccess) return cleanup_fail("cudaMalloc order", e);
+  if ((e = cudaMalloc(&P->d_twiddles, std::max<size_t>(1, tw_pool.size()) * sizeof(float2))) != cudaSuccess) return cleanup_fail("cudaMalloc twiddles", e);
+  if ((e = cudaMalloc(&P->d_counter, sizeof(int))) != cudaSuccess) return cleanup_fail("cudaMalloc counter", e);
+  if (batch > 0) {
+    if ((e = cudaMemcpy(P->d_shapes, P->shapes.data(), P->shapes.size() * sizeof(Shape), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload shapes", e);
+    if ((e = cudaMemcpy(P->d_sig_shape, P->sig_shape.data(), batch * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload sig_shape", e);
+    if ((e = cudaMemcpy(P->d_sig_T, P->sig_T.data(), batch * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload sig_T", e);
+    if ((e = cudaMemcpy(P->d_order, P->order.data(), batch * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload order", e);
+    if ((e = cudaMemcpy(P->d_twiddles, tw_pool.data(), tw_pool.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload twiddles", e);
+  }
+
+  // kernel attributes and the persistent grid
+  fpssft_status st = dispatch_D(D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    cudaError_t e2 = ensure_dynamic_smem((const void*)k_recover<DD>, P->smem);
+    if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(k_recover): ") + cudaGetErrorString(e2));
+    int per_sm = 0;
+    e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover<DD>, P->threads, P->smem);
+    if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e2));
+    if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
+    if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
+    P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
+    const size_t ls = line_smem(DD, P->L_max);
+    if (ls > (size_t)optin) return fail(FPSSFT_ERR_UNSUPPORTED, "lines exceed shared memory");
+    e2 = ensure_dynamic_smem((const void*)k_project<DD>, ls);
+    if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_adjoint_project<DD>, ls);
+    if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_synth<DD>, ls / 2);
+    const size_t ds = (size_t)P->p.k_cap * (sizeof(float2) + (DD + 1) * sizeof(int)) + (size_t)2 * (1 << P->hash_bits) * sizeof(int);
+    if (e2 == cudaSuccess && ds <= (size_t)optin) e2 = ensure_dynamic_smem((const void*)k_decode<DD>, ds);
+    if (e2 == cudaSuccess && ds <= (size_t)optin) e2 = ensure_dynamic_smem((const void*)k_finalize<DD>, ds);
+    if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e2));
+    return FPSSFT_OK;
+  });
+  if (st != FPSSFT_OK) {
+    const std::string msg = g_last_error;
+    free_plan_memory(P);
+    delete P;
+    return fail(st, msg);
+  }
+  *out = P;
+  return FPSSFT_OK;
+}
+
+extern "C" fpssft_status fpssft_plan(fpssft_plan_t* out, int D, int batch, const int64_t* dims,
+                                     const fpssft_params* params) {
+  return fpssft_plan_create(out, D, batch, dims, params);
+}
+
+extern "C" void fpssft_plan_destroy(fpssft_plan_t plan) {
+  if (!plan) return;
+  free_plan_memory(plan);
+  delete plan;
+}
+
+extern "C" fpssft_status fpssft_plan_get_info(fpssft_plan_t P, fpssft_plan_info* info) {
+  if (!P || !info) return fail(FPSSFT_ERR_INVALID, "null plan or info");
+  info->D = P->D;
+  info->batch = P->batch;
+  info->L_max = P->L_max;
+  info->T_max = P->T_max;
+  info->k_cap = P->p.k_cap;
+  info->hash_cap = 1 << P->hash_bits;
+  info->n_shapes = P->n_shapes;
+  info->threads = P->threads;
+  info->grid = P->grid;
+  info->smem_bytes = (int)P->smem;
+  info->twiddles_in_smem = P->tw_smem ? 1 : 0;
+  return FPSSFT_OK;
+}
+
+extern "C" fpssft_status fpssft_plan_get_lengths(fpssft_plan_t P, int32_t* L_out, int32_t* T_out) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  for (int b = 0; b < P->batch; ++b) {
+    if (L_out) L_out[b] = P->sig_L[b];
+    if (T_out) T_out[b] = P->sig_T[b];
+  }
+  return FPSSFT_OK;
+}
+
+// ================================================================================================
+// Host side: launches
+// ================================================================================================
+
+static int unit_grid(const fpssft_plan_s* P, long long units, int per_sm) {
+  const long long cap = (long long)P->sm_count * per_sm;
+  return (int)std::max(1LL, std::min(units, cap));
+}
+
+static fpssft_status launch_project(fpssft_plan_t P, const void* cubes, const int64_t* offsets,
+                                    const int32_t* alpha, const int32_t* tau, int n_sched, void* out,
+                                    void* stream, int dft) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (n_sched < 0) return fail(FPSSFT_ERR_INVALID, "n_sched must be >= 0");
+  if (P->batch == 0 || n_sched == 0) return FPSSFT_OK;
+  if (!cubes || !offsets || !alpha || !tau || !out) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  ProjectArgs A;
+  A.cubes = static_cast<const float2*>(cubes);
+  A.offsets = offsets;
+  A.alpha = alpha;
+  A.tau = tau;
+  A.n_sched = n_sched;
+  A.tab = P->tables();
+  A.batch = P->batch;
+  A.L_max = P->L_max;
+  A.dft = dft;
+  A.out = static_cast<float2*>(out);
+  const int grid = unit_grid(P, (long long)P->batch * n_sched, 8);
+  const size_t sm = line_smem(P->D, P->L_max);
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    k_project<DD><<<grid, 256, sm, static_cast<cudaStream_t>(stream)>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+extern "C" fpssft_status fpssft_project(fpssft_plan_t P, const void* cubes, const int64_t* offsets,
+                                        const int32_t* alpha, const int32_t* tau, int n_sched, void* bins,
+                                        void* stream) {
+  return launch_project(P, cubes, offsets, alpha, tau, n_sched, bins, stream, 1);
+}
+
+extern "C" fpssft_status fpssft_lines(fpssft_plan_t P, const void* cubes, const int64_t* offsets,
+                                      const int32_t* alpha, const int32_t* tau, int n_sched, void* lines,
+                                      void* stream) {
+  return launch_project(P, cubes, offsets, alpha, tau, n_sched, lines, stream, 0);
+}
+
+extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, const int64_t* offsets,
+                                        const int32_t* alpha, const int32_t* tau, const int32_t* init_count,
+                                        int32_t* out_k, void* out_a, int32_t* out_count, int32_t* out_iters,
+                                        int32_t* out_status, void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (P->batch == 0) return FPSSFT_OK;
+  if (!cubes || !offsets || !alpha || !tau || !out_k || !out_a || !out_count || !out_iters || !out_status)
+    return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RecoverArgs A;
+  A.cubes = static_cast<const float2*>(cubes);
+  A.offsets = offsets;
+  A.alpha = alpha;
+  A.tau = tau;
+  A.sched_stride = P->T_max * P->D;
+  A.tab = P->tables();
+  A.work_counter = P->d_counter;
+  A.batch = P->batch;
+  A.k_cap = P->p.k_cap;
+  A.hash_bits = P->hash_bits;
+  A.L_max = P->L_max;
+  A.tw_smem = P->tw_smem ? 1 : 0;
+  A.early_stop = P->p.early_stop;
+  A.th = P->thresholds();
+  A.init_count = init_count;
+  A.out_k = out_k;
+  A.out_a = static_cast<float2*>(out_a);
+  A.out_count = out_count;
+  A.out_iters = out_iters;
+  A.out_status = out_status;
+  FPSSFT_CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    k_recover<DD><<<P->grid, P->threads, P->smem, s>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+extern "C" fpssft_status fpssft_recover_host(fpssft_plan_t P, const void* cubes, const int64_t* offsets,
+                                             const int32_t* alpha, const int32_t* tau, const int32_t* init_count,
+                                             int32_t* out_k, void* out_a, int32_t* out_count, int32_t* out_iters,
+                                             int32_t* out_status, void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (P->batch == 0) return FPSSFT_OK;
+  if (!cubes || !offsets || !alpha || !tau || !out_k || !out_a || !out_count || !out_iters || !out_status)
+    return fail(FPSSFT_ERR_INVALID, "null host pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t B = (size_t)P->batch, D = (size_t)P->D, kc = (size_t)P->p.k_cap;
+  size_t elems = 0;
+  for (size_t b = 0; b < B; ++b) {
+    if (offsets[b] < 0) return fail(FPSSFT_ERR_INVALID, "negative offset");
+    elems = std::max(elems, (size_t)offsets[b] + (size_t)P->shapes[P->sig_shape[b]].N);
+  }
+  const size_t sched = B * (size_t)P->T_max * D;
+  auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, std::max<size_t>(bytes, 16)); };
+  if (P->st_cubes != nullptr && elems > P->st_cubes_elems) {
+    cudaFree(P->st_cubes);
+    P->st_cubes = nullptr;
+    P->st_cubes_elems = 0;
+    if (alloc(&P->st_cubes, elems * sizeof(float2)) != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, "staging allocation failed");
+    P->st_cubes_elems = elems;
+  }
+  if (P->st_offsets == nullptr) {
+    cudaError_t e = cudaSuccess;
+    if (P->st_cubes == nullptr) {
+      e = alloc(&P->st_cubes, std::max(elems, P->total_elems) * sizeof(float2));
+      P->st_cubes_elems = std::max(elems, P->total_elems);
+    }
+    if (e == cudaSuccess) e = alloc((void**)&P->st_offsets, B * sizeof(int64_t));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_alpha, sched * sizeof(int32_t));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_tau, sched * sizeof(int32_t));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_init, B * sizeof(int32_t));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_k, B * kc * D * sizeof(int32_t));
+    if (e == cudaSuccess) e = alloc(&P->st_a, B * kc * sizeof(float2));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_count, B * sizeof(int32_t));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_iters, B * sizeof(int32_t));
+    if (e == cudaSuccess) e = alloc((void**)&P->st_status, B * sizeof(int32_t));
+    if (e != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, std::string("staging allocation: ") + cudaGetErrorString(e));
+  }
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_cubes, cubes, elems * sizeof(float2), cudaMemcpyHostToDevice, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_offsets, offsets, B * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_alpha, alpha, sched * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_tau, tau, sched * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  const int32_t* dinit = nullptr;
+  if (init_count) {
+    FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_init, init_count, B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_k, out_k, B * kc * D * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_a, out_a, B * kc * sizeof(float2), cudaMemcpyHostToDevice, s));
+    dinit = P->st_init;
+  }
+  fpssft_status st = fpssft_recover(P, P->st_cubes, P->st_offsets, P->st_alpha, P->st_tau, dinit, P->st_k, P->st_a,
+                                    P->st_count, P->st_iters, P->st_status, stream);
+  if (st != FPSSFT_OK) return st;
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_k, P->st_k, B * kc * D * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_a, P->st_a, B * kc * sizeof(float2), cudaMemcpyDeviceToHost, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_count, P->st_count, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_iters, P->st_iters, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_status, P->st_status, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FPSSFT_CUDA_TRY(cudaStreamSynchronize(s));
+  return FPSSFT_OK;
+}
+
+extern "C" fpssft_status fpssft_synth(fpssft_plan_t P, const int32_t* alpha, const int32_t* tau, int n_sched,
+                                      const int32_t* k, const void* a, const int32_t* count, int accumulate,
+                                      void* bins, void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (n_sched < 0 || accumulate < -1 || accumulate > 1) return fail(FPSSFT_ERR_INVALID, "bad n_sched or accumulate");
+  if (P->batch == 0 || n_sched == 0) return FPSSFT_OK;
+  if (!alpha || !tau || !k || !a || !count || !bins) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  SynthArgs A;
+  A.alpha = alpha;
+  A.tau = tau;
+  A.n_sched = n_sched;
+  A.tab = P->tables();
+  A.batch = P->batch;
+  A.L_max = P->L_max;
+  A.k_cap = P->p.k_cap;
+  A.k = k;
+  A.a = static_cast<const float2*>(a);
+  A.count = count;
+  A.accumulate = accumulate;
+  A.bins = static_cast<float2*>(bins);
+  const int grid = unit_grid(P, (long long)P->batch * n_sched, 8);
+  const size_t sm = line_smem(P->D, P->L_max) / 2;
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    k_synth<DD><<<grid, 256, sm, static_cast<cudaStream_t>(stream)>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+extern "C" fpssft_status fpssft_decode(fpssft_plan_t P, const void* bins, const int32_t* alpha, const int32_t* tau,
+                                       int32_t* k, void* a, int32_t* count, int32_t* t0_count, int32_t* status,
+                                       void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (P->batch == 0) return FPSSFT_OK;
+  if (!bins || !alpha || !tau || !k || !a || !count || !t0_count || !status) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  DecodeArgs A;
+  A.bins = static_cast<const float2*>(bins);
+  A.alpha = alpha;
+  A.tau = tau;
+  A.tab = P->tables();
+  A.batch = P->batch;
+  A.L_max = P->L_max;
+  A.k_cap = P->p.k_cap;
+  A.hash_bits = P->hash_bits;
+  A.th = P->thresholds();
+  A.k = k;
+  A.a = static_cast<float2*>(a);
+  A.count = count;
+  A.t0_count = t0_count;
+  A.status = status;
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    const size_t ds = (size_t)P->p.k_cap * (sizeof(float2) + (DD + 1) * sizeof(int)) + (size_t)2 * (1 << P->hash_bits) * sizeof(int);
+    k_decode<DD><<<unit_grid(P, P->batch, 8), 256, ds, static_cast<cudaStream_t>(stream)>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+extern "C" fpssft_status fpssft_finalize(fpssft_plan_t P, int32_t* k, void* a, int32_t* count, void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (P->batch == 0) return FPSSFT_OK;
+  if (!k || !a || !count) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  FinalizeArgs A;
+  A.tab = P->tables();
+  A.batch = P->batch;
+  A.k_cap = P->p.k_cap;
+  A.sort_cap = 1 << P->hash_bits;
+  A.th0sq = P->thresholds().th0sq;
+  A.k = k;
+  A.a = static_cast<float2*>(a);
+  A.count = count;
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    const size_t ds = (size_t)P->p.k_cap * (sizeof(float2) + (DD + 1) * sizeof(int)) + (size_t)2 * (1 << P->hash_bits) * sizeof(int);
+    k_finalize<DD><<<unit_grid(P, P->batch, 8), 256, ds, static_cast<cudaStream_t>(stream)>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+extern "C" fpssft_status fpssft_adjoint(fpssft_plan_t P, fpssft_adj_mode mode, const void* grad_bins,
+                                        const int64_t* offsets, const int32_t* alpha, const int32_t* tau, int n_sched,
+                                        const int32_t* k, const int32_t* count, void* grad_out, void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (n_sched < 0) return fail(FPSSFT_ERR_INVALID, "n_sched must be >= 0");
+  if (mode != FPSSFT_ADJ_PROJECT && mode != FPSSFT_ADJ_SYNTH) return fail(FPSSFT_ERR_INVALID, "unknown adjoint mode");
+  if (P->batch == 0) return FPSSFT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (mode == FPSSFT_ADJ_PROJECT) {
+    if (n_sched == 0) return FPSSFT_OK;
+    if (!grad_bins || !offsets || !alpha || !tau || !grad_out) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+    AdjProjectArgs A;
+    A.g = static_cast<const float2*>(grad_bins);
+    A.offsets = offsets;
+    A.alpha = alpha;
+    A.tau = tau;
+    A.n_sched = n_sched;
+    A.tab = P->tables();
+    A.batch = P->batch;
+    A.L_max = P->L_max;
+    A.grad = static_cast<float2*>(grad_out);
+    const int grid = unit_grid(P, (long long)P->batch * n_sched, 8);
+    const size_t sm = line_smem(P->D, P->L_max);
+    return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+      constexpr int DD = decltype(Dc)::value;
+      k_adjoint_project<DD><<<grid, 256, sm, s>>>(A);
+      FPSSFT_CUDA_TRY(cudaGetLastError());
+      return FPSSFT_OK;
+    });
+  }
+  if (!grad_bins || !alpha || !tau || !k || !count || !grad_out) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  AdjSynthArgs A;
+  A.g = static_cast<const float2*>(grad_bins);
+  A.alpha = alpha;
+  A.tau = tau;
+  A.n_sched = n_sched;
+  A.tab = P->tables();
+  A.batch = P->batch;
+  A.L_max = P->L_max;
+  A.k_cap = P->p.k_cap;
+  A.k = k;
+  A.count = count;
+  A.grad_a = static_cast<float2*>(grad_out);
+  const long long total = (long long)P->batch * P->p.k_cap;
+  const int grid = (int)std::max(1LL, std::min((total + 255) / 256, (long long)P->sm_count * 16));
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    k_adjoint_synth<DD><<<grid, 256, 0, s>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+extern "C" const char* fpssft_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* fpssft_version(void) { return "fpssft-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,474 @@
+// Device building blocks of the FPS-SFT recovery loop (sm_103a).
+//
+// Paper: Wang, Patel, Petropulu, "FPS-SFT: A Multi-dimensional Sparse Fourier Transform Based on
+// the Fourier Projection-slice Theorem", arXiv 1711.11407.
+//
+// Everything here works on one signal per CTA: the D+1 lines of one iteration live in shared
+// memory as [D+1][L] complex64 (line-major), the recovered set lives in shared memory as a dense
+// list plus an open-addressing index, and every phase ends with a CTA barrier issued by the
+// caller.  Integer work (grid points, bins, twiddle indices) is exact; bins are FP32; the
+// 1-sparsity tests and the phase decode are evaluated in FP64 from the FP32 bins.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fpssft {
+
+constexpr int kMaxD = 4;
+constexpr int kMaxStages = 24;
+constexpr int kEmpty = -1;           // empty hash slot (keys are linear indices >= 0)
+
+// One distinct cube shape of a batch, with its line length and FFT factorisation.
+struct Shape {
+  int D;
+  int L;                     // LCM of the dims (Lemma 1)
+  int N;                     // number of grid points
+  int nst;                   // FFT stages
+  int tw_off;                // offset of the L-entry twiddle table in the pool
+  int pad_;
+  int dims[kMaxD];
+  int strides[kMaxD];        // row-major element strides (last dimension fastest)
+  int c[kMaxD];              // L / N_d
+  int radix[kMaxStages];     // radices, product = L
+};
+
+// True when every component lies on the grid (0 <= k_d < N_d); entries that fail are skipped by
+// every kernel that reads caller-supplied frequencies.
+template <int D>
+__device__ __forceinline__ bool on_grid(const Shape& sh, const int* k) {
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) ok = ok && k[d] >= 0 && k[d] < sh.dims[d];
+  return ok;
+}
+
+// [c_d v]_L in [0, L) for any int v (schedule entries are reduced, never trusted to be in range).
+__device__ __forceinline__ int cmod(int c, int v, int L) {
+  long long r = ((long long)c * (long long)v) % L;
+  return (int)(r < 0 ? r + L : r);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul_mj(float2 a) { return make_float2(a.y, -a.x); }   // a * (-j)
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ------------------------------------------------------------------------------------------------
+// a1: gather the D+1 lines (Eq. sample_slice; offsets tau and tau + e_d, Sec. 2.3)
+// ------------------------------------------------------------------------------------------------
+// buf[j * L + l] = x(n_j(l)),  n_d(l) = [alpha_d l + tau_d]_{N_d},  line d+1 adds e_d (mod N_d).
+// One thread owns one l and issues the D+1 loads of that l back to back; line D (offset on the
+// fastest dimension) is the neighbour of line 0 in memory and usually shares its 32-byte sector.
+template <int D>
+__device__ __forceinline__ void gather_lines(float2* __restrict__ buf, const float2* __restrict__ x,
+                                             const Shape& sh, const int* __restrict__ alpha,
+                                             const int* __restrict__ tau) {
+  const int L = sh.L;
+  int al[D], ta[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { al[d] = __ldg(alpha + d); ta[d] = __ldg(tau + d); }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    int n[D];
+    int base = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      n[d] = (int)(((unsigned)al[d] * (unsigned)l + (unsigned)ta[d]) % (unsigned)sh.dims[d]);
+      base += n[d] * sh.strides[d];
+    }
+    float2 v[D + 1];
+    v[0] = __ldg(x + base);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int step = (n[d] + 1 == sh.dims[d]) ? -(sh.dims[d] - 1) * sh.strides[d] : sh.strides[d];
+      v[d + 1] = __ldg(x + base + step);
+    }
+#pragma unroll
+    for (int j = 0; j <= D; ++j) buf[j * L + l] = v[j];
+  }
+}
+
+// Grid-point address of line j at position l (used by the projection adjoint's scatter).
+template <int D>
+__device__ __forceinline__ int line_address(const Shape& sh, const int* al, const int* ta, int j, int l) {
+  int base = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int nd = (int)(((unsigned)al[d] * (unsigned)l + (unsigned)ta[d] + (unsigned)(j == d + 1)) % (unsigned)sh.dims[d]);
+    base += nd * sh.strides[d];
+  }
+  return base;
+}
+
+// ------------------------------------------------------------------------------------------------
+// a2: L-point DFT of every line (Eq. hs), mixed-radix Stockham in shared memory
+// ------------------------------------------------------------------------------------------------
+// Stage with radix R and span Ns (product of the earlier radices): butterfly j of a line reads
+// in[j + i L/R], multiplies input i by w^(i (j mod Ns) L/(Ns R)) with w = exp(-j 2 pi / L), takes the
+// R-point DFT and writes out[(j - j mod Ns) R + j mod Ns + i Ns].  After all stages the output is
+// in natural order.  tw[q] = exp(-j 2 pi q / L), computed in FP64 on the host and rounded to FP32.
+template <int R>
+__device__ __forceinline__ void butterfly(float2 (&v)[R]);
+
+template <>
+__device__ __forceinline__ void butterfly<2>(float2 (&v)[2]) {
+  const float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<3>(float2 (&v)[3]) {
+  const float h = 0.86602540378443865f;  // sin(2 pi / 3)
+  const float2 t1 = cadd(v[1], v[2]);
+  const float2 t2 = csub(v[1], v[2]);
+  const float2 m = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+  const float2 n = cscale(mul_mj(t2), h);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, n);
+  v[2] = csub(m, n);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<4>(float2 (&v)[4]) {
+  const float2 t0 = cadd(v[0], v[2]);
+  const float2 t1 = csub(v[0], v[2]);
+  const float2 t2 = cadd(v[1], v[3]);
+  const float2 t3 = mul_mj(csub(v[1], v[3]));
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[3] = csub(t1, t3);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<5>(float2 (&v)[5]) {
+  const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;   // cos(2 pi/5), cos(4 pi/5)
+  const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;    // sin(2 pi/5), sin(4 pi/5)
+  const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  const float2 a0 = v[0];
+  const float2 b1 = make_float2(a0.x + c1 * t1.x + c2 * t2.x, a0.y + c1 * t1.y + c2 * t2.y);
+  const float2 b2 = make_float2(a0.x + c2 * t1.x + c1 * t2.x, a0.y + c2 * t1.y + c1 * t2.y);
+  const float2 e1 = mul_mj(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+  const float2 e2 = mul_mj(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+  v[0] = cadd(a0, cadd(t1, t2));
+  v[1] = cadd(b1, e1);
+  v[4] = csub(b1, e1);
+  v[2] = cadd(b2, e2);
+  v[3] = csub(b2, e2);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<8>(float2 (&v)[8]) {
+  const float c = 0.70710678118654752f;
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  butterfly<4>(e);
+  butterfly<4>(o);
+  // o[q] *= exp(-j 2 pi q / 8)
+  o[1] = make_float2(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x));
+  o[2] = mul_mj(o[2]);
+  o[3] = make_float2(c * (o[3].y - o[3].x), -c * (o[3].x + o[3].y));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = cadd(e[q], o[q]);
+    v[q + 4] = csub(e[q], o[q]);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2* __restrict__ out, int L,
+                                          int nlines, int Ns, const float2* __restrict__ tw, float sc) {
+  const int nb = L / R;
+  const int tstep = L / (Ns * R);
+  const int total = nlines * nb;
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    const int line = w / nb;
+    const int j = w - line * nb;
+    const float2* src = in + line * L;
+    float2* dst = out + line * L;
+    const int k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = src[j + i * nb];
+    if (k != 0) {
+#pragma unroll
+      for (int i = 1; i < R; ++i) v[i] = cmul(v[i], tw[i * k * tstep]);
+    }
+    butterfly<R>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int i = 0; i < R; ++i) dst[base + i * Ns] = cscale(v[i], sc);
+  }
+}
+
+// Any radix (used for prime factors other than 2, 3, 5): O(R^2) per butterfly, inputs re-read
+// from shared memory.
+__device__ __forceinline__ void fft_stage_generic(const float2* __restrict__ in, float2* __restrict__ out,
+                                                  int L, int nlines, int Ns, int R,
+                                                  const float2* __restrict__ tw, float sc) {
+  const int nb = L / R;
+  const int tstep = L / (Ns * R);
+  const int rstep = L / R;           // exp(-j 2 pi x / R) = tw[(x mod R) * L / R]
+  const int total = nlines * nb;
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    const int line = w / nb;
+    const int j = w - line * nb;
+    const float2* src = in + line * L;
+    float2* dst = out + line * L;
+    const int k = j % Ns;
+    const int base = (j - k) * R + k;
+    for (int q = 0; q < R; ++q) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int i = 0; i < R; ++i) {
+        float2 v = src[j + i * nb];
+        if (k != 0 && i != 0) v = cmul(v, tw[i * k * tstep]);
+        acc = cadd(acc, cmul(v, tw[((i * q) % R) * rstep]));
+      }
+      dst[base + q * Ns] = cscale(acc, sc);
+    }
+  }
+}
+
+// Forward DFT (exp(-j ...)) of nlines contiguous lines of length sh.L held in buf0, scaled by
+// `scale` at the last stage; buf1 is the ping-pong partner.  Ends with a barrier after each stage
+// and returns the buffer holding the result.
+__device__ __forceinline__ float2* fft_lines(float2* buf0, float2* buf1, int nlines, const Shape& sh,
+                                             const float2* __restrict__ tw, float scale) {
+  float2* in = buf0;
+  float2* out = buf1;
+  int Ns = 1;
+  const int L = sh.L;
+  for (int s = 0; s < sh.nst; ++s) {
+    const int R = sh.radix[s];
+    const float sc = (s == sh.nst - 1) ? scale : 1.f;
+    switch (R) {
+      case 2: fft_stage<2>(in, out, L, nlines, Ns, tw, sc); break;
+      case 3: fft_stage<3>(in, out, L, nlines, Ns, tw, sc); break;
+      case 4: fft_stage<4>(in, out, L, nlines, Ns, tw, sc); break;
+      case 5: fft_stage<5>(in, out, L, nlines, Ns, tw, sc); break;
+      case 8: fft_stage<8>(in, out, L, nlines, Ns, tw, sc); break;
+      default: fft_stage_generic(in, out, L, nlines, Ns, R, tw, sc); break;
+    }
+    __syncthreads();
+    float2* t = in;
+    in = out;
+    out = t;
+    Ns *= R;
+  }
+  return in;
+}
+
+// ------------------------------------------------------------------------------------------------
+// The recovered set: dense list + open-addressing index (a5)
+// ------------------------------------------------------------------------------------------------
+struct SetView {
+  int* lk;        // [D][k_cap] frequency components
+  int* lkey;      // [k_cap] row-major linear index
+  float2* la;     // [k_cap] amplitudes
+  int* hkey;      // [hash_cap] key or kEmpty
+  int* hidx;      // [hash_cap] list position (-1: key claimed by an insert that overflowed)
+  int* count;     // entries appended (may exceed k_cap after an overflow; clamp when reading)
+  int k_cap;
+  int hash_bits;
+};
+
+__device__ __forceinline__ unsigned hash_slot(int key, int bits) {
+  return ((unsigned)key * 2654435761u) >> (32 - bits);
+}
+
+// Insert (k, a) or add a to the existing entry of key.  Within one iteration every key comes from
+// at most one bin (the bin of k is unique), so concurrent calls carry distinct keys and an existing
+// key was inserted (and fully written) in an earlier iteration.  Returns false on overflow.
+template <int D>
+__device__ __forceinline__ bool set_insert(const SetView& s, const int* k, int key, float2 a) {
+  const unsigned mask = (1u << s.hash_bits) - 1u;
+  unsigned h = hash_slot(key, s.hash_bits);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(&s.hkey[h], kEmpty, key);
+    if (old == kEmpty) {
+      const int idx = atomicAdd(s.count, 1);
+      if (idx >= s.k_cap) {
+        s.hidx[h] = -1;
+        return false;
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) s.lk[d * s.k_cap + idx] = k[d];
+      s.lkey[idx] = key;
+      s.la[idx] = a;
+      s.hidx[h] = idx;
+      return true;
+    }
+    if (old == key) {
+      const int idx = s.hidx[h];
+      if (idx < 0) return false;
+      s.la[idx] = cadd(s.la[idx], a);
+      return true;
+    }
+    h = (h + 1u) & mask;
+  }
+  return false;   // unreachable at load factor <= 1/2
+}
+
+// ------------------------------------------------------------------------------------------------
+// a3: peel -- subtract the recovered set's bins (Eq. freqSum over the set, Sec. 2.2)
+// ------------------------------------------------------------------------------------------------
+// For entry (k, a): m = [sum_d ca_d k_d]_L with ca_d = [c_d alpha_d]_L; p = [sum_d ct_d k_d]_L with
+// ct_d = [c_d tau_d]_L; line 0 gets a W^p and line d+1 gets a W^(p + c_d k_d), W = exp(j 2 pi / L)
+// (conj of the forward table).  sign = -1 subtracts (peel), +1 adds (synthesis).
+template <int D>
+__device__ __forceinline__ void project_entry(float2* bins, int line_stride, const Shape& sh, const int* k,
+                                              float2 a, const int* ca, const int* ct,
+                                              const float2* __restrict__ tw, float sign) {
+  const int L = sh.L;
+  int msum = 0, psum = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    msum += ca[d] * k[d];
+    psum += ct[d] * k[d];
+  }
+  const int m = msum % L;
+  const int p = psum % L;
+  float2 v = cmulc(a, tw[p]);
+  atomicAdd(&bins[m].x, sign * v.x);
+  atomicAdd(&bins[m].y, sign * v.y);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int q = p + sh.c[d] * k[d];
+    if (q >= L) q -= L;
+    v = cmulc(a, tw[q]);
+    atomicAdd(&bins[(d + 1) * line_stride + m].x, sign * v.x);
+    atomicAdd(&bins[(d + 1) * line_stride + m].y, sign * v.y);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void peel_set(float2* bins, const Shape& sh, const SetView& s, int count,
+                                         const int* ca, const int* ct, const float2* __restrict__ tw) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int k[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) k[d] = s.lk[d * s.k_cap + i];
+    project_entry<D>(bins, sh.L, sh, k, s.la[i], ca, ct, tw, -1.f);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// a4 + a5: 1-sparsity tests, OFDM-trick decode (Eq. decoding) and merge
+// ------------------------------------------------------------------------------------------------
+struct Thresholds {
+  double th0sq;    // theta0^2
+  double rho;
+  double eta;
+};
+
+// Tests T0..T3 on every bin m of the (already peeled) lines; bins of line j at bins[j*line_stride].
+// Adds the number of line-0 bins passing T0 to *t0 and sets *ovf on a capacity overflow.
+template <int D>
+__device__ __forceinline__ void decode_bins(const float2* bins, int line_stride, const Shape& sh,
+                                            const SetView& s, const int* ca, const int* ct,
+                                            const float2* __restrict__ tw, const Thresholds& th,
+                                            int* t0, int* ovf) {
+  const int L = sh.L;
+  const double kTwoPi = 6.283185307179586476925286766559;
+  int my_t0 = 0;
+  bool my_ovf = false;
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    const float2 s0 = bins[m];
+    const double e0 = (double)s0.x * s0.x + (double)s0.y * s0.y;
+    if (!(e0 > th.th0sq)) continue;                                   // T0
+    ++my_t0;
+    const double r0 = sqrt(e0);
+    float2 sd[D];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      sd[d] = bins[(d + 1) * line_stride + m];
+      const double e = (double)sd[d].x * sd[d].x + (double)sd[d].y * sd[d].y;
+      if (fabs(sqrt(e) - r0) > th.rho * r0) ok = false;               // T1
+    }
+    if (!ok) continue;
+    int k[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      // phase of s_{d+1} / s_0, taken as the phase of s_{d+1} conj(s_0) (FP64 products are exact)
+      const double re = (double)sd[d].x * s0.x + (double)sd[d].y * s0.y;
+      const double im = (double)sd[d].y * s0.x - (double)sd[d].x * s0.y;
+      const double u = (double)sh.dims[d] * atan2(im, re) / kTwoPi;
+      const double r = floor(u + 0.5);
+      if (fabs(u - r) > th.eta) ok = false;                           // T2
+      int kd = (int)r % sh.dims[d];
+      if (kd < 0) kd += sh.dims[d];
+      k[d] = kd;
+    }
+    if (!ok) continue;
+    int msum = 0, psum = 0, key = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      msum += ca[d] * k[d];
+      psum += ct[d] * k[d];
+      key += k[d] * sh.strides[d];
+    }
+    if (msum % L != m) continue;                                      // T3
+    const float2 a = cmul(s0, tw[psum % L]);                          // a = s_0 W^-p
+    if (!set_insert<D>(s, k, key, a)) my_ovf = true;
+  }
+  if (my_t0) atomicAdd(t0, my_t0);
+  if (my_ovf) atomicOr(ovf, 1);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Output: drop |a| <= theta0 and sort by linear index (bitonic sort in shared memory)
+// ------------------------------------------------------------------------------------------------
+// skey/sidx need pow2ceil(count) entries.  Returns the number of kept entries (in *n_out) with
+// sidx[r] the list position of the r-th smallest key.
+__device__ __forceinline__ void sort_kept(const SetView& s, int count, double th0sq, int* skey, int* sidx,
+                                          int* n_out) {
+  if (threadIdx.x == 0) *n_out = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const float2 a = s.la[i];
+    if ((double)a.x * a.x + (double)a.y * a.y > th0sq) {
+      const int pos = atomicAdd(n_out, 1);
+      skey[pos] = s.lkey[i];
+      sidx[pos] = i;
+    }
+  }
+  __syncthreads();
+  const int n = *n_out;
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
+    skey[i] = 0x7fffffff;
+    sidx[i] = -1;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const int ki = skey[i], kj = skey[ixj];
+          if ((ki > kj) == up) {
+            skey[i] = kj;
+            skey[ixj] = ki;
+            const int t = sidx[i];
+            sidx[i] = sidx[ixj];
+            sidx[ixj] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace fpssft

@@ -1,0 +1,68 @@
+"""The C ABI library: builds for sm_103a, loads, exports every declared symbol, and rejects bad
+arguments on the host before touching a device (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1711_11407_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "fpssft.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fpssft_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function():
+    lib = _lib.load()
+    names = declared_functions()
+    assert len(names) >= 14
+    raw = ctypes.CDLL(_lib.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), f"{n} declared in include/fpssft.h but not exported"
+    assert set(names) == set(_lib.SIGNATURES), "binding signatures must cover exactly the declared functions"
+    assert lib.fpssft_version().startswith(b"fpssft")
+
+
+def _plan(D, batch, dims, **kw):
+    lib = _lib.load()
+    p = _lib.CParams(kw.get("T", 10), kw.get("k_cap", 64), kw.get("theta0", 1e-3), 1e-3, 0.05, 1,
+                     kw.get("peel_mode", 0), kw.get("threads", 0), 0)
+    h = ctypes.c_void_p()
+    d = np.ascontiguousarray(np.asarray(dims, np.int64).reshape(-1))
+    st = lib.fpssft_plan_create(ctypes.byref(h), D, batch, d.ctypes.data_as(ctypes.c_void_p) if d.size else None,
+                                ctypes.byref(p))
+    return st, lib.fpssft_last_error().decode()
+
+
+@pytest.mark.parametrize("D,batch,dims,kw,expect", [
+    (0, 1, [4], {}, _lib.ERR_INVALID),
+    (5, 1, [2, 2, 2, 2, 2], {}, _lib.ERR_INVALID),
+    (2, -1, [], {}, _lib.ERR_INVALID),
+    (2, 1, [0, 4], {}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"k_cap": 0}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"T": -1}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"theta0": -1.0}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"threads": 48}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"threads": 1024}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
+    (2, 1, [4096, 3], {}, _lib.ERR_UNSUPPORTED),            # L = 12288 lines exceed one CTA
+    (2, 1, [65536, 65536], {}, _lib.ERR_UNSUPPORTED),       # N >= 2^31
+])
+def test_plan_validation_on_host(D, batch, dims, kw, expect):
+    st, msg = _plan(D, batch, dims, **kw)
+    assert st == expect, msg
+    assert msg, "a failing call leaves a message"
+
+
+def test_null_plan_rejected():
+    lib = _lib.load()
+    assert lib.fpssft_recover(None, *([None] * 11)) == _lib.ERR_INVALID
+    assert lib.fpssft_project(None, None, None, None, None, 1, None, None) == _lib.ERR_INVALID
+    assert lib.fpssft_adjoint(None, 0, None, None, None, None, 1, None, None, None, None) == _lib.ERR_INVALID
+    assert b"null plan" in lib.fpssft_last_error()

@@ -1,0 +1,325 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI (needs a GB300).
+
+Tolerances: integer work (gathered samples, frequency indices, iteration counts, status) is
+compared exactly; FP32 line bins within 1e-5 relative L2 per line; amplitudes within 1e-4 relative
+per entry.  The oracle receives the same complex64 cube (upcast to complex128) and the same
+schedule."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fpssft_oracle as O
+from paper_1711_11407_gb300 import configs
+from paper_1711_11407_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+BIN_TOL = 1e-5
+AMP_TOL = 1e-4
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def to_dev(wl):
+    d = dev()
+    return (torch.from_numpy(wl.cubes).to(d), torch.from_numpy(wl.offsets).to(d),
+            torch.from_numpy(wl.alpha).to(d), torch.from_numpy(wl.tau).to(d))
+
+
+def oracle_params(p, T):
+    return O.Params(T=T, k_cap=p.k_cap, theta0=p.theta0, rho=p.rho, eta=p.eta, early_stop=p.early_stop)
+
+
+def assert_same_set(k, a, ref, ctx=""):
+    assert k.shape == ref.k.shape and np.array_equal(k, ref.k), f"support differs from the oracle {ctx}"
+    err = np.abs(a - ref.a)
+    assert np.all(err <= AMP_TOL * np.maximum(np.abs(ref.a), 1e-30)), f"amplitude error {err.max()} {ctx}"
+
+
+def small_batch(shapes, batch, K, T, seed=7, snr_db=None):
+    return S.make_workload("uneven_2d", seed=seed, batch=batch, shapes=shapes, K=K, T=T, snr_db=snr_db)
+
+
+SHAPE_SETS = {
+    "D1": [(16,), (30,), (7,), (64,)],
+    "D2-ragged": [(6, 10), (5, 7), (1, 16), (7, 11), (12, 18), (64, 64)],
+    "D2-large": [(128, 128), (240, 256), (256, 256)],
+    "D3": [(4, 6, 3), (8, 8, 8), (5, 3, 2), (64, 64, 64)],
+    "D4": [(4, 4, 2, 3), (2, 3, 2, 5)],
+}
+
+
+@pytest.mark.parametrize("name", sorted(SHAPE_SETS))
+def test_lines_are_exact_copies_of_the_oracle_samples(name):
+    from paper_1711_11407_gb300.api import Plan
+    wl = small_batch(SHAPE_SETS[name], 12, K=lambda N: min(4, N), T=3)
+    plan = Plan(wl.dims)
+    cubes, offs, al, ta = to_dev(wl)
+    lines = plan.lines(cubes, offs, al, ta).cpu().numpy()
+    for b in range(wl.batch):
+        L = int(plan.L[b])
+        for s in range(wl.alpha.shape[1]):
+            ref = O.sample_lines(wl.cube(b), wl.alpha[b, s], wl.tau[b, s])
+            got = lines[b, s, :, :L].astype(np.complex128)
+            assert np.array_equal(got, ref), f"gathered samples differ: signal {b} dims {wl.dims[b]} row {s}"
+            assert np.all(lines[b, s, :, L:] == 0)
+
+
+@pytest.mark.parametrize("name", sorted(SHAPE_SETS))
+def test_project_matches_oracle_line_dft(name):
+    from paper_1711_11407_gb300.api import Plan
+    wl = small_batch(SHAPE_SETS[name], 10, K=lambda N: min(6, N), T=3, snr_db=0.0)   # noisy: dense bins
+    plan = Plan(wl.dims)
+    cubes, offs, al, ta = to_dev(wl)
+    bins = plan.project(cubes, offs, al, ta).cpu().numpy()
+    worst = 0.0
+    for b in range(wl.batch):
+        L = int(plan.L[b])
+        for s in range(wl.alpha.shape[1]):
+            ref = O.project(wl.cube(b), wl.alpha[b, s], wl.tau[b, s])
+            for j in range(wl.D + 1):
+                e = np.linalg.norm(bins[b, s, j, :L] - ref[j]) / max(np.linalg.norm(ref[j]), 1e-30)
+                worst = max(worst, e)
+                assert e <= BIN_TOL, f"line bins rel L2 {e:.2e} > {BIN_TOL}: dims {wl.dims[b]} line {j}"
+            assert np.all(bins[b, s, :, L:] == 0)
+    print(f"worst line-bin relative L2 error: {worst:.2e}")
+
+
+RECOVER_CASES = {
+    "config1_single_128x128": lambda: S.make_workload("single_128x128"),
+    "config2_single_240x256": lambda: S.make_workload("single_240x256"),
+    "uneven_2d_48": lambda: S.make_workload("uneven_2d", batch=48),
+    "D3_16cubed": lambda: small_batch([(16, 16, 16)], 6, K=lambda N: 30, T=20),
+    "D1": lambda: small_batch([(64,), (60,), (7,)], 6, K=lambda N: min(5, N // 2), T=6),
+    "D4": lambda: small_batch([(4, 4, 4, 6)], 4, K=lambda N: 4, T=10),
+    "D2-ragged": lambda: small_batch([(6, 10), (5, 7), (7, 11), (12, 18), (1, 16)], 10, K=lambda N: max(1, min(4, N // 8)), T=12),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RECOVER_CASES))
+def test_recover_matches_oracle(case):
+    from paper_1711_11407_gb300.api import Plan
+    wl = RECOVER_CASES[case]()
+    if case.startswith("D"):     # small batches with a fixed schedule length
+        p = configs.params_for(wl, T=int(wl.alpha.shape[1]), k_cap=64)
+    else:
+        p = configs.params_for(wl)
+    plan = Plan(wl.dims, p)
+    cubes, offs, al, ta = to_dev(wl)
+    out = plan.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    for b in range(wl.batch):
+        T = int(plan.T[b])
+        ref = O.recover(wl.cube(b), wl.alpha[b, :T], wl.tau[b, :T], oracle_params(p, T))
+        k, a = out.signal(b)
+        assert_same_set(k, a, ref, f"signal {b} dims {wl.dims[b]}")
+        assert int(out.iters[b]) == ref.iters, f"iterations {int(out.iters[b])} vs oracle {ref.iters}"
+        assert int(out.status[b]) == ref.status
+
+
+def test_recover_full_uneven_batch_sampled_against_oracle():
+    """4096 uneven 2-D signals in the launch configuration the benchmark times; 40 sampled signals
+    against the oracle, every signal against its planted spectrum."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d")
+    p = configs.params_for(wl)
+    plan = Plan(wl.dims, p)
+    cubes, offs, al, ta = to_dev(wl)
+    out = plan.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    ks, as_, cnt = out.k.cpu().numpy(), out.a.cpu().numpy(), out.count.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for b in rng.choice(wl.batch, 40, replace=False):
+        T = int(plan.T[b])
+        ref = O.recover(wl.cube(b), wl.alpha[b, :T], wl.tau[b, :T], oracle_params(p, T))
+        assert_same_set(ks[b, :cnt[b]].astype(np.int64), as_[b, :cnt[b]].astype(np.complex128), ref, f"signal {b}")
+        assert int(out.iters[b]) == ref.iters
+    ok = 0
+    for b in range(wl.batch):
+        dims = tuple(int(v) for v in wl.dims[b])
+        truth = np.sort(O.linear_index(wl.k_true[b], dims))
+        got = O.linear_index(ks[b, :cnt[b]].astype(np.int64), dims)
+        ok += int(np.array_equal(got, truth))
+    assert ok / wl.batch >= 0.999, f"exact-support success {ok}/{wl.batch}"
+    assert np.all(out.status.cpu().numpy() == 0)
+
+
+def test_synth_peel_and_adjoints_match_oracle():
+    from paper_1711_11407_gb300.api import Plan
+    wl = small_batch([(6, 10), (16, 24), (240, 256), (7, 11)], 8, K=lambda N: min(12, N // 2), T=3, snr_db=3.0)
+    plan = Plan(wl.dims, configs.params_for(wl, k_cap=32))
+    cubes, offs, al, ta = to_dev(wl)
+    B, kc, D, Lm = wl.batch, plan.k_cap, wl.D, plan.L_max
+    rng = np.random.default_rng(3)
+    k = np.zeros((B, kc, D), np.int32)
+    a = np.zeros((B, kc), np.complex64)
+    cnt = np.zeros(B, np.int32)
+    for b in range(B):
+        n = min(len(wl.k_true[b]), kc)
+        k[b, :n] = wl.k_true[b][:n]
+        a[b, :n] = (rng.normal(size=n) + 1j * rng.normal(size=n)).astype(np.complex64)
+        cnt[b] = n
+    kd, ad, cd = torch.from_numpy(k).to(dev()), torch.from_numpy(a).to(dev()), torch.from_numpy(cnt).to(dev())
+    syn = plan.synth(al, ta, kd, ad, cd).cpu().numpy()
+    bins = plan.project(cubes, offs, al, ta)
+    peeled = plan.synth(al, ta, kd, ad, cd, accumulate=-1, bins=bins.clone()).cpu().numpy()
+    g = (rng.normal(size=(B, 3, D + 1, Lm)) + 1j * rng.normal(size=(B, 3, D + 1, Lm))).astype(np.complex64)
+    gd = torch.from_numpy(g).to(dev())
+    grad_cube = plan.adjoint_project(gd, offs, al, ta, torch.zeros_like(cubes)).cpu().numpy()
+    grad_a = plan.adjoint_synth(gd, al, ta, kd, cd).cpu().numpy()
+    bins = bins.cpu().numpy()
+    for b in range(B):
+        L = int(plan.L[b])
+        dims = tuple(int(v) for v in wl.dims[b])
+        n = cnt[b]
+        acc_cube = np.zeros(dims, np.complex128)
+        acc_a = np.zeros(n, np.complex128)
+        for s in range(3):
+            ref = O.synth(k[b, :n], a[b, :n].astype(np.complex128), wl.alpha[b, s], wl.tau[b, s], dims)
+            e = np.linalg.norm(syn[b, s, :, :L] - ref) / np.linalg.norm(ref)
+            assert e <= BIN_TOL, f"synth rel L2 {e:.2e}"
+            refp = O.project(wl.cube(b), wl.alpha[b, s], wl.tau[b, s]) - ref
+            e = np.linalg.norm(peeled[b, s, :, :L] - refp) / np.linalg.norm(refp)
+            assert e <= BIN_TOL, f"peel rel L2 {e:.2e}"
+            gg = g[b, s, :, :L].astype(np.complex128)
+            acc_cube += O.project_adjoint(gg, wl.alpha[b, s], wl.tau[b, s], dims)
+            acc_a += O.synth_adjoint(gg, k[b, :n], wl.alpha[b, s], wl.tau[b, s], dims)
+        o = int(wl.offsets[b])
+        gc = grad_cube[o:o + int(np.prod(dims))].reshape(dims)
+        e = np.linalg.norm(gc - acc_cube) / np.linalg.norm(acc_cube)
+        assert e <= BIN_TOL, f"projection adjoint rel L2 {e:.2e}"
+        e = np.linalg.norm(grad_a[b, :n] - acc_a) / np.linalg.norm(acc_a)
+        assert e <= BIN_TOL, f"synthesis adjoint rel L2 {e:.2e}"
+        # dot-product test on the GPU's own forward/adjoint pair
+        lhs = np.vdot(g[b, :, :, :L].astype(np.complex128), bins[b, :, :, :L].astype(np.complex128))
+        rhs = np.vdot(gc, wl.cube(b))
+        assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+def test_unfused_per_signal_form_equals_fused_kernel():
+    from paper_1711_11407_gb300.api import Plan
+    from paper_1711_11407_gb300.plain import PlainRecoverer
+    wl = S.make_workload("uneven_2d", batch=12)
+    p = configs.params_for(wl)
+    plan = Plan(wl.dims, p)
+    cubes, offs, al, ta = to_dev(wl)
+    out = plan.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    res = PlainRecoverer(p).recover(wl, cubes, al, ta, range(wl.batch))
+    for b, (k, a, it, st) in enumerate(res):
+        kf, af = out.signal(b)
+        assert np.array_equal(k, kf) and np.allclose(a, af, rtol=AMP_TOL, atol=0)
+        assert it == int(out.iters[b]) and st == int(out.status[b])
+
+
+def test_resume_one_iteration_at_a_time_equals_one_run():
+    """Checkpoint/resume: T single-iteration calls chained through init_count reach the same set."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("single_240x256")
+    p = configs.params_for(wl)
+    full = Plan(wl.dims, p)
+    cubes, offs, al, ta = to_dev(wl)
+    ref = full.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    step = Plan(wl.dims, configs.params_for(wl, T=1))
+    out = step.alloc_output()
+    init = torch.zeros(1, dtype=torch.int32, device=dev())
+    for t in range(int(ref.iters[0])):
+        step.recover(cubes, offs, al[:, t:t + 1].contiguous(), ta[:, t:t + 1].contiguous(), out=out, init_count=init)
+        init.copy_(out.count)
+    torch.cuda.synchronize()
+    k1, a1 = ref.signal(0)
+    k2, a2 = out.signal(0)
+    assert np.array_equal(k1, k2) and np.allclose(a1, a2, rtol=AMP_TOL, atol=0)
+
+
+def test_teacher_forced_noisy_iterations_match_oracle():
+    """Noisy 64^3 cube: feed the oracle's set before iteration t to both sides and compare what one
+    iteration adds (decisions on noisy bins, compared one iteration at a time)."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("batched_64x64x64", batch=2)
+    p = configs.params_for(wl, T=1)
+    plan = Plan(wl.dims, p)
+    cubes, offs, al, ta = to_dev(wl)
+    for b in range(wl.batch):
+        x = wl.cube(b)
+        for t in (0, 3, 10):
+            prev = O.recover(x, wl.alpha[b], wl.tau[b], oracle_params(p, t), T=t) if t else None
+            init_k = prev.k if prev is not None else np.zeros((0, 3), np.int64)
+            init_a = prev.a if prev is not None else np.zeros(0, np.complex128)
+            nxt = O.recover(x, wl.alpha[b, t:t + 1], wl.tau[b, t:t + 1], oracle_params(p, 1), init=(init_k, init_a), T=1)
+            out = plan.alloc_output()
+            n0 = init_k.shape[0]
+            kk = np.zeros((wl.batch, plan.k_cap, 3), np.int32)
+            aa = np.zeros((wl.batch, plan.k_cap), np.complex64)
+            kk[b, :n0] = init_k
+            aa[b, :n0] = init_a
+            out.k.copy_(torch.from_numpy(kk))
+            out.a.copy_(torch.from_numpy(aa))
+            init = torch.zeros(wl.batch, dtype=torch.int32, device=dev())
+            init[b] = n0
+            plan.recover(cubes, offs, al[:, t:t + 1].contiguous(), ta[:, t:t + 1].contiguous(), out=out, init_count=init)
+            torch.cuda.synchronize()
+            k, a = out.signal(b)
+            assert np.array_equal(k, nxt.k), f"teacher-forced iteration {t} of cube {b}: support differs"
+            assert np.allclose(a, nxt.a, rtol=1e-3, atol=0)
+
+
+def test_capacity_overflow_reports_status_and_keeps_k_cap_entries():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("single_128x128")
+    p = configs.params_for(wl, k_cap=8)
+    plan = Plan(wl.dims, p)
+    out = plan.recover(*to_dev(wl))
+    torch.cuda.synchronize()
+    ref = O.recover(wl.cube(0), wl.alpha[0], wl.tau[0], oracle_params(p, p.T))
+    assert int(out.status[0]) == O.STATUS_CAPACITY == ref.status
+    assert int(out.count[0]) == ref.k.shape[0] == 8
+    assert int(out.iters[0]) == ref.iters
+
+
+def test_recover_host_buffers_equal_device_buffers():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=64)
+    p = configs.params_for(wl)
+    plan = Plan(wl.dims, p)
+    dv = plan.recover(*to_dev(wl))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        hv = plan.recover_host(wl.cubes, wl.offsets, wl.alpha, wl.tau)
+        assert torch.equal(hv.count, dv.count.cpu()) and torch.equal(hv.iters, dv.iters.cpu())
+        for b in range(wl.batch):
+            n = int(hv.count[b])
+            assert torch.equal(hv.k[b, :n], dv.k[b, :n].cpu())
+            assert torch.allclose(hv.a[b, :n], dv.a[b, :n].cpu(), rtol=AMP_TOL, atol=0)
+
+
+def test_empty_batch_is_a_no_op():
+    from paper_1711_11407_gb300.api import Plan
+    plan = Plan(np.zeros((0, 2), np.int64))
+    e = torch.zeros(0, dtype=torch.complex64, device=dev())
+    z = torch.zeros((0, plan.T_max, 2), dtype=torch.int32, device=dev())
+    out = plan.recover(e, torch.zeros(0, dtype=torch.int64, device=dev()), z, z)
+    torch.cuda.synchronize()
+    assert out.count.numel() == 0
+
+
+def test_plans_of_different_sizes_coexist():
+    """A later plan with shorter lines must not lower the shared-memory limit of an earlier plan's
+    kernels (the limit is per kernel, shared by all plans)."""
+    from paper_1711_11407_gb300.api import Plan
+    big = S.make_workload("single_240x256")
+    small = small_batch([(8, 8)], 2, K=lambda N: 2, T=3)
+    p_big = Plan(big.dims, configs.params_for(big))
+    Plan(small.dims, configs.params_for(small, T=3, k_cap=8))
+    cubes, offs, al, ta = to_dev(big)
+    p_big.project(cubes, offs, al, ta)
+    out = p_big.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    ref = O.recover(big.cube(0), big.alpha[0], big.tau[0], oracle_params(configs.params_for(big), 12))
+    k, a = out.signal(0)
+    assert_same_set(k, a, ref)
