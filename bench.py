@@ -42,7 +42,7 @@ UNIT = "signals/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fpssft", choices=["fpssft", "reference"])
     ap.add_argument("--workload", default="uneven_2d")
@@ -107,47 +107,63 @@ def profiled_traffic(workload, batch):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region: the sampler starts before it
+    (and its first line is awaited), every line is time-stamped on arrival, and the summary keeps
+    the lines that arrived between begin() and end()."""
 
     FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid):
+    def __init__(self, uuid, period_ms=50):
+        import threading
         self.uuid = uuid
+        self.lines = []
+        self.t0 = self.t1 = None
         self.proc = None
-
-    def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "-lms", str(period_ms)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
         except Exception:
-            self.proc = None
-        return self
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        deadline = time.monotonic() + 5.0
+        while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
 
-    def __exit__(self, *exc):
-        self.out = ""
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
+
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
+        time.sleep(0.12)     # let the sample that covers the end of the region arrive
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                self.out = ""
 
     def summary(self):
         rows = []
-        for r in csv.reader(io.StringIO(getattr(self, "out", ""))):
-            r = [c.strip() for c in r]
-            if len(r) < 10:
+        for t, line in self.lines:
+            if self.t0 is None or not (self.t0 <= t <= self.t1 + 0.1):
                 continue
-            if self.uuid and self.uuid not in r[1]:
+            r = [c.strip() for c in next(csv.reader([line]))]
+            if len(r) < 10 or (self.uuid and self.uuid not in r[1]):
                 continue
             rows.append(r)
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no sample inside the timed region"], "samples": 0}
+        num = lambda v: float(v) if v.replace(".", "", 1).isdigit() else None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
@@ -263,13 +279,18 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        with ClockSampler(uuid) as clk:
-            for i in range(args.steps):
-                flush.zero_()
-                ev[i][0].record(stream)
-                run()
-                ev[i][1].record(stream)
-            torch.cuda.synchronize()
+        clk = ClockSampler(uuid)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.begin()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            run()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk.end()
         if world > 1:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in ev]

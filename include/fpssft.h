@@ -73,6 +73,9 @@ typedef struct {
   int peel_mode;     /* 0 = subtract the recovered set's projections from the bins (only mode) */
   int threads;       /* CTA size of the recovery kernel; 0 = library default */
   int ctas_per_sm;   /* resident CTAs per SM for the persistent recovery grid; 0 = occupancy */
+  int fp64_decisions;/* nonzero: evaluate T0..T2 in FP64 for every bin.  0 (default): evaluate in
+                        FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a
+                        guard band around a threshold -- the verdicts are the same either way */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;

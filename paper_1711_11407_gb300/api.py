@@ -26,10 +26,12 @@ class Params:
     peel_mode: int = 0
     threads: int = 0
     ctas_per_sm: int = 0
+    fp64_decisions: bool = False
 
     def c(self):
         return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
-                            int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm))
+                            int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
+                            int(bool(self.fp64_decisions)))
 
 
 @dataclass

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
 
     // output: keep |a| > theta0, sorted by linear index (hash arrays reused as sort buffers)
     const int count = min(s_count, A.k_cap);
-    sort_kept(set, count, A.th.th0sq, set.hkey, set.hidx, &s_n);
+    sort_kept(set, count, A.th, set.hkey, set.hidx, &s_n);
     const int n = s_n;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
       const int i = set.hidx[r];
@@ -430,7 +430,7 @@ struct FinalizeArgs {
   int batch;
   int k_cap;
   int sort_cap;     // power of two >= k_cap
-  double th0sq;
+  Thresholds th;
   int* k;
   float2* a;
   int* count;
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeArgs A) {
       set.la[i] = A.a[(size_t)b * A.k_cap + i];
     }
     __syncthreads();
-    sort_kept(set, n0, A.th0sq, skey, sidx, &s_n);
+    sort_kept(set, n0, A.th, skey, sidx, &s_n);
     const int n = s_n;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
       const int i = sidx[r];
@@ -629,10 +629,26 @@ struct fpssft_plan_s {
 
   DeviceTables tables() const { return DeviceTables{d_shapes, d_sig_shape, d_sig_T, d_order, d_twiddles}; }
   Thresholds thresholds() const {
+    // FP32 guard bands: 1e-6 relative on either side of each FP64 threshold (FP32 evaluation
+    // error <= 3e-7 relative), rounded outward to the next float.
+    auto up = [](double v) { float f = (float)v; return (double)f < v ? std::nextafter(f, INFINITY) : f; };
+    auto down = [](double v) { float f = (float)v; return (double)f > v ? std::nextafter(f, -INFINITY) : f; };
+    const double g = 1e-6;
     Thresholds t;
     t.th0sq = (double)p.theta0 * (double)p.theta0;
     t.rho = p.rho;
     t.eta = p.eta;
+    t.t0_lo = down(t.th0sq * (1.0 - g));
+    t.t0_hi = up(t.th0sq * (1.0 + g));
+    const double hi2 = (1.0 + t.rho) * (1.0 + t.rho);
+    const double lo = std::max(0.0, 1.0 - t.rho);
+    const double lo2 = lo * lo;
+    t.t1_hi_pass = down(hi2 * (1.0 - 2 * g));
+    t.t1_hi_fail = up(hi2 * (1.0 + 2 * g));
+    t.t1_lo_pass = lo2 > 0 ? up(lo2 * (1.0 + 2 * g)) : 0.f;
+    t.t1_lo_fail = lo2 > 0 ? down(lo2 * (1.0 - 2 * g)) : -1.f;
+    t.eta_f = (float)t.eta;
+    t.fp64_all = p.fp64_decisions ? 1 : 0;
     return t;
   }
 };
@@ -1123,7 +1139,7 @@ extern "C" fpssft_status fpssft_finalize(fpssft_plan_t P, int32_t* k, void* a, i
   A.batch = P->batch;
   A.k_cap = P->p.k_cap;
   A.sort_cap = 1 << P->hash_bits;
-  A.th0sq = P->thresholds().th0sq;
+  A.th = P->thresholds();
   A.k = k;
   A.a = static_cast<float2*>(a);
   A.count = count;

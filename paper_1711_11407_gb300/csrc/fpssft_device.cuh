@@ -363,11 +363,93 @@ __device__ __forceinline__ void peel_set(float2* bins, const Shape& sh, const Se
 // ------------------------------------------------------------------------------------------------
 // a4 + a5: 1-sparsity tests, OFDM-trick decode (Eq. decoding) and merge
 // ------------------------------------------------------------------------------------------------
+// The decisions T0..T2 are defined in FP64 on the FP32 bins.  GB300 runs FP64 at a small
+// fraction of its FP32 rate, so every bin is first evaluated in FP32 and the FP32 verdict is used
+// only when it is certified: the FP32 value lies outside a guard band around the threshold that is
+// wider than the largest possible FP32-vs-FP64 difference (FP32 products and sums: relative error
+// <= 2^-23; atan2f: <= 3 ulp by the CUDA math library's documented bound; the band keeps a factor
+// >= 4 on top).  Bins inside a band are re-evaluated entirely in FP64, so every verdict equals the
+// one a pure FP64 evaluation gives.  fp64_all = 1 forces the FP64 evaluation for every bin.
 struct Thresholds {
-  double th0sq;    // theta0^2
+  double th0sq;      // theta0^2
   double rho;
   double eta;
+  float t0_lo, t0_hi;              // e0 < t0_lo: T0 fails; e0 > t0_hi: T0 passes (e0 = |s_0|^2 in FP32)
+  float t1_hi_pass, t1_hi_fail;    // e <= t1_hi_pass e0: upper T1 bound holds; e > t1_hi_fail e0: fails
+  float t1_lo_pass, t1_lo_fail;    // e >= t1_lo_pass e0: lower T1 bound holds; e < t1_lo_fail e0: fails
+  float eta_f;
+  int fp64_all;
 };
+
+// Verdicts: 1 = every test passes (k filled), -1 = rejected, 0 = not certified in FP32.
+constexpr int kAccept = 1, kReject = -1, kUndecided = 0;
+
+template <int D>
+__device__ __forceinline__ int classify_fp32(const float2 s0, const float2* sd, const Shape& sh,
+                                             const Thresholds& th, int* k, bool* t0_counted) {
+  const float kInvTwoPi = 0.159154943091895336f;
+  const float kPiGuard = 3.14158f;                 // |phi| closer to pi than this: wrap side uncertain
+  const float e0 = fmaf(s0.x, s0.x, s0.y * s0.y);
+  if (e0 < th.t0_lo) return kReject;               // T0 fails
+  if (!(e0 > th.t0_hi)) return kUndecided;
+  *t0_counted = true;                              // T0 passes
+  bool undecided = false;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {                    // T1
+    const float e = fmaf(sd[d].x, sd[d].x, sd[d].y * sd[d].y);
+    if (e > th.t1_hi_fail * e0 || e < th.t1_lo_fail * e0) return kReject;
+    if (!(e <= th.t1_hi_pass * e0 && e >= th.t1_lo_pass * e0)) undecided = true;
+  }
+  if (undecided) return kUndecided;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {                    // decode + T2
+    const float re = fmaf(sd[d].x, s0.x, sd[d].y * s0.y);
+    const float im = fmaf(sd[d].y, s0.x, -(sd[d].x * s0.y));
+    const float phi = atan2f(im, re);
+    if (fabsf(phi) > kPiGuard) return kUndecided;
+    const float nd = (float)sh.dims[d];
+    const float u = nd * phi * kInvTwoPi;
+    const float r = floorf(u + 0.5f);
+    const float dist = fabsf(u - r);
+    const float band = 2e-6f * nd + 1e-6f;
+    if (fabsf(dist - th.eta_f) <= band || fabsf(dist - 0.5f) <= band) return kUndecided;
+    if (dist > th.eta_f) return kReject;
+    int kd = (int)r % sh.dims[d];
+    if (kd < 0) kd += sh.dims[d];
+    k[d] = kd;
+  }
+  return kAccept;
+}
+
+template <int D>
+__device__ __forceinline__ int classify_fp64(const float2 s0, const float2* sd, const Shape& sh,
+                                             const Thresholds& th, int* k, bool* t0_counted) {
+  const double kTwoPi = 6.283185307179586476925286766559;
+  const double e0 = (double)s0.x * s0.x + (double)s0.y * s0.y;
+  if (!(e0 > th.th0sq)) return kReject;                               // T0
+  *t0_counted = true;
+  const double r0 = sqrt(e0);
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double e = (double)sd[d].x * sd[d].x + (double)sd[d].y * sd[d].y;
+    if (fabs(sqrt(e) - r0) > th.rho * r0) ok = false;                 // T1
+  }
+  if (!ok) return kReject;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    // phase of s_{d+1} / s_0, taken as the phase of s_{d+1} conj(s_0) (FP64 products are exact)
+    const double re = (double)sd[d].x * s0.x + (double)sd[d].y * s0.y;
+    const double im = (double)sd[d].y * s0.x - (double)sd[d].x * s0.y;
+    const double u = (double)sh.dims[d] * atan2(im, re) / kTwoPi;
+    const double r = floor(u + 0.5);
+    if (fabs(u - r) > th.eta) ok = false;                             // T2
+    int kd = (int)r % sh.dims[d];
+    if (kd < 0) kd += sh.dims[d];
+    k[d] = kd;
+  }
+  return ok ? kAccept : kReject;
+}
 
 // Tests T0..T3 on every bin m of the (already peeled) lines; bins of line j at bins[j*line_stride].
 // Adds the number of line-0 bins passing T0 to *t0 and sets *ovf on a capacity overflow.
@@ -377,38 +459,23 @@ __device__ __forceinline__ void decode_bins(const float2* bins, int line_stride,
                                             const float2* __restrict__ tw, const Thresholds& th,
                                             int* t0, int* ovf) {
   const int L = sh.L;
-  const double kTwoPi = 6.283185307179586476925286766559;
   int my_t0 = 0;
   bool my_ovf = false;
   for (int m = threadIdx.x; m < L; m += blockDim.x) {
     const float2 s0 = bins[m];
-    const double e0 = (double)s0.x * s0.x + (double)s0.y * s0.y;
-    if (!(e0 > th.th0sq)) continue;                                   // T0
-    ++my_t0;
-    const double r0 = sqrt(e0);
     float2 sd[D];
-    bool ok = true;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      sd[d] = bins[(d + 1) * line_stride + m];
-      const double e = (double)sd[d].x * sd[d].x + (double)sd[d].y * sd[d].y;
-      if (fabs(sqrt(e) - r0) > th.rho * r0) ok = false;               // T1
-    }
-    if (!ok) continue;
+    for (int d = 0; d < D; ++d) sd[d] = bins[(d + 1) * line_stride + m];
     int k[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      // phase of s_{d+1} / s_0, taken as the phase of s_{d+1} conj(s_0) (FP64 products are exact)
-      const double re = (double)sd[d].x * s0.x + (double)sd[d].y * s0.y;
-      const double im = (double)sd[d].y * s0.x - (double)sd[d].x * s0.y;
-      const double u = (double)sh.dims[d] * atan2(im, re) / kTwoPi;
-      const double r = floor(u + 0.5);
-      if (fabs(u - r) > th.eta) ok = false;                           // T2
-      int kd = (int)r % sh.dims[d];
-      if (kd < 0) kd += sh.dims[d];
-      k[d] = kd;
+    bool counted = false;
+    int v = th.fp64_all ? kUndecided : classify_fp32<D>(s0, sd, sh, th, k, &counted);
+    if (v == kUndecided) {
+      bool c64 = false;
+      v = classify_fp64<D>(s0, sd, sh, th, k, &c64);
+      counted = c64;
     }
-    if (!ok) continue;
+    my_t0 += counted ? 1 : 0;
+    if (v != kAccept) continue;
     int msum = 0, psum = 0, key = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -424,18 +491,27 @@ __device__ __forceinline__ void decode_bins(const float2* bins, int line_stride,
   if (my_ovf) atomicOr(ovf, 1);
 }
 
+// |a|^2 > theta0^2, certified in FP32 when outside the guard band, else in FP64.
+__device__ __forceinline__ bool keep_amplitude(float2 a, const Thresholds& th) {
+  if (!th.fp64_all) {
+    const float e = fmaf(a.x, a.x, a.y * a.y);
+    if (e < th.t0_lo) return false;
+    if (e > th.t0_hi) return true;
+  }
+  return (double)a.x * a.x + (double)a.y * a.y > th.th0sq;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Output: drop |a| <= theta0 and sort by linear index (bitonic sort in shared memory)
 // ------------------------------------------------------------------------------------------------
 // skey/sidx need pow2ceil(count) entries.  Returns the number of kept entries (in *n_out) with
 // sidx[r] the list position of the r-th smallest key.
-__device__ __forceinline__ void sort_kept(const SetView& s, int count, double th0sq, int* skey, int* sidx,
-                                          int* n_out) {
+__device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thresholds& th, int* skey,
+                                          int* sidx, int* n_out) {
   if (threadIdx.x == 0) *n_out = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    const float2 a = s.la[i];
-    if ((double)a.x * a.x + (double)a.y * a.y > th0sq) {
+    if (keep_amplitude(s.la[i], th)) {
       const int pos = atomicAdd(n_out, 1);
       skey[pos] = s.lkey[i];
       sidx[pos] = i;
