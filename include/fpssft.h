@@ -76,6 +76,9 @@ typedef struct {
   int fp64_decisions;/* nonzero: evaluate T0..T2 in FP64 for every bin.  0 (default): evaluate in
                         FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a
                         guard band around a threshold -- the verdicts are the same either way */
+  int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice, 1 = synchronous
+                        through L1, 2 = synchronous cached in L2 only, 3 = asynchronous copies of
+                        the next iteration's lines while the current one computes */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;
@@ -92,6 +95,7 @@ typedef struct {
   int grid;           /* persistent CTAs launched by fpssft_recover */
   int smem_bytes;     /* dynamic shared memory per recovery CTA */
   int twiddles_in_smem;
+  int prefetch;       /* 1: the next iteration's lines are gathered while the current one computes */
 } fpssft_plan_info;
 
 /* Create a plan for `batch` signals of dimension D with shapes dims (HOST int64 [batch][D],
@@ -189,6 +193,22 @@ fpssft_status fpssft_adjoint(fpssft_plan_t plan, fpssft_adj_mode mode, const voi
                              const int64_t* offsets, const int32_t* alpha, const int32_t* tau,
                              int n_sched, const int32_t* k, const int32_t* count, void* grad_out,
                              void* stream);
+
+/* Measurement helper (no counterpart in the paper): the random-gather ceiling the line gather is
+ * compared against.  threads_total threads each read reads_per_thread 8-byte elements at
+ * pseudo-random positions of buf (device, n_elems complex64 elements, a power of two; use a
+ * buffer much larger than L2), plus the following element when pair = 1, and write one complex64
+ * per thread to out (device, threads_total elements).  load_mode 0 loads through L1
+ * (ld.global.nc), 1 caches in L2 only (ld.global.cg).  Asynchronous on stream. */
+fpssft_status fpssft_probe_gather(const void* buf, int64_t n_elems, int reads_per_thread, int threads_total,
+                                  int load_mode, int pair, void* out, void* stream);
+
+/* The line gather reads isolated 8-byte samples; by default the memory system may fetch a whole
+ * 128-byte line from DRAM for each.  This sets the current device's L2 fetch-granularity hint
+ * (cudaLimitMaxL2FetchGranularity: 0, 32, 64 or 128 bytes) for the calling process's context --
+ * it affects every kernel of the process and nothing outside it -- and returns the previous value
+ * in *previous (nullable).  bytes < 0 only queries. */
+fpssft_status fpssft_l2_fetch_granularity(int bytes, int* previous);
 
 /* Message of the last failed call on this thread ("" when none). */
 const char* fpssft_last_error(void);

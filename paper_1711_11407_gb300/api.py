@@ -27,11 +27,12 @@ class Params:
     threads: int = 0
     ctas_per_sm: int = 0
     fp64_decisions: bool = False
+    gather_mode: int = 0
 
     def c(self):
         return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
                             int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
-                            int(bool(self.fp64_decisions)))
+                            int(bool(self.fp64_decisions)), int(self.gather_mode))
 
 
 @dataclass
@@ -216,3 +217,23 @@ class Plan:
         _lib.check(self.lib.fpssft_adjoint(self.handle, _lib.ADJ_SYNTH, _ptr(grad_bins), None, _ptr(alpha),
                                            _ptr(tau), S, _ptr(k), _ptr(count), _ptr(grad_a), _stream(stream)))
         return grad_a
+
+
+def probe_gather(buf, reads_per_thread=64, threads_total=152 * 8 * 256, load_mode=0, pair=0, stream=None):
+    """Random 8-byte gathers over `buf` (complex64 CUDA tensor, power-of-two length); returns the
+    output tensor (one complex64 per thread).  Time it with CUDA events around the call."""
+    lib = _lib.load()
+    _need(buf, torch.complex64, "buf")
+    out = torch.empty(threads_total, dtype=torch.complex64, device=buf.device)
+    _lib.check(lib.fpssft_probe_gather(_ptr(buf), buf.numel(), int(reads_per_thread), int(threads_total),
+                                       int(load_mode), int(pair), _ptr(out), _stream(stream)))
+    return out
+
+
+def l2_fetch_granularity(nbytes=-1):
+    """Set the process's L2 fetch-granularity hint (0/32/64/128 bytes; < 0 only queries); returns
+    the previous value."""
+    lib = _lib.load()
+    prev = ctypes.c_int(0)
+    _lib.check(lib.fpssft_l2_fetch_granularity(int(nbytes), ctypes.byref(prev)))
+    return prev.value

@@ -87,6 +87,8 @@ struct RecoverArgs {
   int hash_bits;
   int L_max;
   int tw_smem;
+  int prefetch;
+  int gather_mode;
   int early_stop;
   Thresholds th;
   const int* init_count;
@@ -98,16 +100,20 @@ struct RecoverArgs {
 };
 
 struct SmemLayout {
-  size_t bufA, bufB, tw, la, lk, lkey, hkey, hidx, total;
+  size_t bufA, bufB, bufC, tw, la, lk, lkey, hkey, hidx, total;
 };
 
-static __host__ __device__ SmemLayout recover_layout(int D, int L_max, int k_cap, int hash_cap, bool tw_smem) {
+// bufA / bufC: the samples of iterations t and t+1 (bufC only when the gather is prefetched);
+// bufB: the FFT's ping-pong partner.
+static __host__ __device__ SmemLayout recover_layout(int D, int L_max, int k_cap, int hash_cap, bool tw_smem,
+                                                     bool prefetch) {
   auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
   SmemLayout s{};
   size_t off = 0;
   const size_t lines = (size_t)(D + 1) * L_max * sizeof(float2);
   s.bufA = off; off = al(off + lines);
   s.bufB = off; off = al(off + lines);
+  s.bufC = off; off = al(off + (prefetch ? lines : 0));
   s.tw = off; off = al(off + (tw_smem ? (size_t)L_max * sizeof(float2) : 0));
   s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
   s.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
@@ -139,9 +145,11 @@ __global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
 
-  const SmemLayout lay = recover_layout(D, A.L_max, A.k_cap, 1 << A.hash_bits, A.tw_smem != 0);
+  const SmemLayout lay = recover_layout(D, A.L_max, A.k_cap, 1 << A.hash_bits, A.tw_smem != 0, A.prefetch != 0);
   float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
   float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
+  float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
+  const bool pf = A.prefetch != 0;
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
   SetView set;
   set.la = reinterpret_cast<float2*>(smem + lay.la);
@@ -194,19 +202,35 @@ __global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
     }
 
     const int T = A.tab.sig_T[b];
+    const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
+    const int* sched_t = A.tau + (size_t)b * A.sched_stride;
+    if (pf && T > 0) gather_lines_async<D>(bufA, x, sh, sched_a, sched_t);
     int iters = 0;
     for (int t = 0; t < T; ++t) {
-      const int* al = A.alpha + (size_t)b * A.sched_stride + t * D;
-      const int* ta = A.tau + (size_t)b * A.sched_stride + t * D;
+      const int* al = sched_a + t * D;
+      const int* ta = sched_t + t * D;
       if (threadIdx.x < D) {
         const int d = threadIdx.x;
-        s_ca[d] = cmod(sh.c[d], al[d], L);
-        s_ct[d] = cmod(sh.c[d], ta[d], L);
+        s_ca[d] = cmodL(sh, d, al[d]);
+        s_ct[d] = cmodL(sh, d, ta[d]);
       }
-      gather_lines<D>(bufA, x, sh, al, ta);
+      float2* cur = (pf && (t & 1)) ? bufC : bufA;
+      if (pf) {
+        // samples of t were requested one iteration ago; request t+1's now, wait for t's
+        if (t + 1 < T) {
+          gather_lines_async<D>((t & 1) ? bufA : bufC, x, sh, al + D, ta + D);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+      } else if (A.gather_mode == 2) {
+        gather_lines<D, 1>(bufA, x, sh, al, ta);
+      } else {
+        gather_lines<D, 0>(bufA, x, sh, al, ta);
+      }
       __syncthreads();
       if (threadIdx.x == 0) s_t0 = 0;
-      float2* bins = fft_lines(bufA, bufB, D + 1, sh, tw, 1.0f / (float)L);
+      float2* bins = fft_lines(cur, bufB, D + 1, sh, tw, 1.0f / (float)L);
       peel_set<D>(bins, sh, set, min(s_count, A.k_cap), s_ca, s_ct, tw);
       __syncthreads();
       decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf);
@@ -216,6 +240,7 @@ __global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
       if (stop) break;
     }
 
+    if (pf) cp_async_wait<0>();   // a prefetch past the last iteration still lands before reuse
     // output: keep |a| > theta0, sorted by linear index (hash arrays reused as sort buffers)
     const int count = min(s_count, A.k_cap);
     sort_kept(set, count, A.th, set.hkey, set.hidx, &s_n);
@@ -319,8 +344,8 @@ __global__ void __launch_bounds__(256) k_synth(SynthArgs A) {
     const int* ta = A.tau + u * D;
     if (threadIdx.x < D) {
       const int d = threadIdx.x;
-      s_ca[d] = cmod(sh.c[d], al[d], L);
-      s_ct[d] = cmod(sh.c[d], ta[d], L);
+      s_ca[d] = cmodL(sh, d, al[d]);
+      s_ct[d] = cmodL(sh, d, ta[d]);
     }
     float2* o = A.bins + u * (D + 1) * (long long)A.L_max;
     for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
@@ -392,8 +417,8 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
     const int L = sh.L;
     if (threadIdx.x < D) {
       const int d = threadIdx.x;
-      s_ca[d] = cmod(sh.c[d], A.alpha[b * D + d], L);
-      s_ct[d] = cmod(sh.c[d], A.tau[b * D + d], L);
+      s_ca[d] = cmodL(sh, d, A.alpha[b * D + d]);
+      s_ct[d] = cmodL(sh, d, A.tau[b * D + d]);
     }
     const int n0 = min(max(A.count[b], 0), A.k_cap);
     for (int i = threadIdx.x; i < n0; i += blockDim.x) {
@@ -520,8 +545,8 @@ __global__ void __launch_bounds__(256) k_adjoint_project(AdjProjectArgs A) {
     int al[D], ta[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      al[d] = A.alpha[u * D + d];
-      ta[d] = A.tau[u * D + d];
+      al[d] = fmod_(A.alpha[u * D + d] & 0x3fffffff, sh.fdims[d]);
+      ta[d] = fmod_(A.tau[u * D + d] & 0x3fffffff, sh.fdims[d]);
     }
     float2* out = A.grad + A.offsets[b];
     for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
@@ -568,8 +593,8 @@ __global__ void __launch_bounds__(256) k_adjoint_synth(AdjSynthArgs A) {
       long long msum = 0, psum = 0;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        msum += (long long)cmod(sh.c[d], A.alpha[u * D + d], L) * k[d];
-        psum += (long long)cmod(sh.c[d], A.tau[u * D + d], L) * k[d];
+        msum += (long long)cmodL(sh, d, A.alpha[u * D + d]) * k[d];
+        psum += (long long)cmodL(sh, d, A.tau[u * D + d]) * k[d];
       }
       const int m = (int)(msum % L);
       const int p = (int)(psum % L);
@@ -603,6 +628,7 @@ struct fpssft_plan_s {
   int grid = 1;
   int sm_count = 1;
   bool tw_smem = true;
+  bool prefetch = true;
   size_t smem = 0;
   size_t total_elems = 0;   // sum of N_b (for host staging)
   std::vector<Shape> shapes;
@@ -654,6 +680,18 @@ struct fpssft_plan_s {
 };
 
 namespace {
+
+FastDiv make_fastdiv(int d) {
+  int l = 0;
+  while ((1LL << l) < d) ++l;
+  const unsigned long long m = ((1ULL << 32) * ((1ULL << l) - (unsigned long long)d)) / (unsigned long long)d + 1ULL;
+  FastDiv f;
+  f.m = (unsigned)m;
+  f.l = l;
+  f.d = d;
+  f.pad_ = 0;
+  return f;
+}
 
 std::vector<int> factorize(int L) {
   std::vector<int> r;
@@ -717,6 +755,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
+  if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
   if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
 
   auto* P = new (std::nothrow) fpssft_plan_s();
@@ -760,7 +799,16 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       auto rad = factorize((int)L);
       if ((int)rad.size() > kMaxStages) { delete P; return fail(FPSSFT_ERR_UNSUPPORTED, "too many FFT stages"); }
       sh.nst = (int)rad.size();
-      for (size_t s = 0; s < rad.size(); ++s) sh.radix[s] = rad[s];
+      for (int d = 0; d < kMaxD; ++d) sh.fdims[d] = make_fastdiv(d < D ? dv[d] : 1);
+      sh.fL = make_fastdiv((int)L);
+      int ns = 1;
+      for (size_t s = 0; s < rad.size(); ++s) {
+        sh.radix[s] = rad[s];
+        sh.tstep[s] = (int)(L / ((long long)ns * rad[s]));
+        sh.fnb[s] = make_fastdiv((int)(L / rad[s]));
+        sh.fns[s] = make_fastdiv(ns);
+        ns *= rad[s];
+      }
       auto t = tw_off.find((int)L);
       if (t == tw_off.end()) {
         const int off = (int)tw_pool.size();
@@ -808,10 +856,18 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (sms <= 0) sms = 1;
   P->sm_count = sms;
   const size_t static_reserve = sizeof(Shape) + 256;
-  SmemLayout lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true);
+  // prefer prefetched gathers (unless a synchronous gather mode is requested) and twiddles in
+  // shared memory; drop them in that order if they do not fit
+  const bool want_pf = pr.gather_mode == 0 || pr.gather_mode == 3;
+  SmemLayout lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, want_pf);
   P->tw_smem = true;
+  P->prefetch = want_pf;
   if (lay.total + static_reserve > (size_t)optin) {
-    lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false);
+    lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, false);
+    P->prefetch = false;
+  }
+  if (lay.total + static_reserve > (size_t)optin) {
+    lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false, false);
     P->tw_smem = false;
   }
   if (lay.total + static_reserve > (size_t)optin) {
@@ -906,6 +962,7 @@ extern "C" fpssft_status fpssft_plan_get_info(fpssft_plan_t P, fpssft_plan_info*
   info->grid = P->grid;
   info->smem_bytes = (int)P->smem;
   info->twiddles_in_smem = P->tw_smem ? 1 : 0;
+  info->prefetch = P->prefetch ? 1 : 0;
   return FPSSFT_OK;
 }
 
@@ -989,6 +1046,8 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   A.hash_bits = P->hash_bits;
   A.L_max = P->L_max;
   A.tw_smem = P->tw_smem ? 1 : 0;
+  A.prefetch = P->prefetch ? 1 : 0;
+  A.gather_mode = P->p.gather_mode;
   A.early_stop = P->p.early_stop;
   A.th = P->thresholds();
   A.init_count = init_count;
@@ -1203,6 +1262,67 @@ extern "C" fpssft_status fpssft_adjoint(fpssft_plan_t P, fpssft_adj_mode mode, c
     FPSSFT_CUDA_TRY(cudaGetLastError());
     return FPSSFT_OK;
   });
+}
+
+// ---- random-gather ceiling ------------------------------------------------------------------
+// Every thread reads `reads` 8-byte elements at pseudo-random positions of a buffer of n = 2^k
+// elements (much larger than L2), optionally together with the next element (the adjacent pair
+// the line gather reads for line 0 and line D), and folds them into one output element so the
+// loads cannot be dropped.  Positions come from a 64-bit mixing function of (thread, read).
+template <int LM, int PAIR>
+__global__ void __launch_bounds__(256) k_probe_gather(const float2* __restrict__ buf, unsigned long long mask,
+                                                      int reads, unsigned long long seed, float2* out) {
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float ax = 0.f, ay = 0.f;
+  unsigned long long h = (tid + 1) * 0x9E3779B97F4A7C15ull ^ seed;
+#pragma unroll 8
+  for (int r = 0; r < reads; ++r) {
+    h += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = h;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const unsigned long long i = z & mask;
+    const float2 v = load_sample<LM>(buf + i);
+    ax += v.x;
+    ay += v.y;
+    if (PAIR) {
+      const float2 w = load_sample<LM>(buf + ((i + 1) & mask));
+      ax += w.x;
+      ay += w.y;
+    }
+  }
+  out[tid] = make_float2(ax, ay);
+}
+
+extern "C" fpssft_status fpssft_probe_gather(const void* buf, int64_t n_elems, int reads_per_thread, int threads_total,
+                                             int load_mode, int pair, void* out, void* stream) {
+  if (!buf || !out) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  if (n_elems < 2 || (n_elems & (n_elems - 1)) != 0) return fail(FPSSFT_ERR_INVALID, "n_elems must be a power of two >= 2");
+  if (reads_per_thread < 1 || threads_total < 256 || threads_total % 256 != 0) return fail(FPSSFT_ERR_INVALID, "bad sizes");
+  if (load_mode < 0 || load_mode > 1 || pair < 0 || pair > 1) return fail(FPSSFT_ERR_INVALID, "bad mode");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned long long mask = (unsigned long long)n_elems - 1;
+  const float2* b = static_cast<const float2*>(buf);
+  float2* o = static_cast<float2*>(out);
+  const int grid = threads_total / 256;
+  const unsigned long long seed = 0x2545F4914F6CDD1Dull;
+  if (load_mode == 0 && pair == 0) k_probe_gather<0, 0><<<grid, 256, 0, s>>>(b, mask, reads_per_thread, seed, o);
+  if (load_mode == 0 && pair == 1) k_probe_gather<0, 1><<<grid, 256, 0, s>>>(b, mask, reads_per_thread, seed, o);
+  if (load_mode == 1 && pair == 0) k_probe_gather<1, 0><<<grid, 256, 0, s>>>(b, mask, reads_per_thread, seed, o);
+  if (load_mode == 1 && pair == 1) k_probe_gather<1, 1><<<grid, 256, 0, s>>>(b, mask, reads_per_thread, seed, o);
+  FPSSFT_CUDA_TRY(cudaGetLastError());
+  return FPSSFT_OK;
+}
+
+extern "C" fpssft_status fpssft_l2_fetch_granularity(int bytes, int* previous) {
+  size_t cur = 0;
+  FPSSFT_CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity));
+  if (previous) *previous = (int)cur;
+  if (bytes < 0) return FPSSFT_OK;
+  if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128) return fail(FPSSFT_ERR_INVALID, "bytes must be 0, 32, 64 or 128");
+  FPSSFT_CUDA_TRY(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes));
+  return FPSSFT_OK;
 }
 
 extern "C" const char* fpssft_last_error(void) { return g_last_error.c_str(); }

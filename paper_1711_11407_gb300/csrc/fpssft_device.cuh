@@ -19,6 +19,21 @@ constexpr int kMaxD = 4;
 constexpr int kMaxStages = 24;
 constexpr int kEmpty = -1;           // empty hash slot (keys are linear indices >= 0)
 
+// Division by a runtime-invariant divisor d >= 1 as a multiply-high and a shift (Granlund and
+// Montgomery's round-up method): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> l for every 0 <= n < 2^31.  The host fills (m, l, d).
+struct FastDiv {
+  unsigned m;
+  int l;
+  int d;
+  int pad_;
+};
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return (int)((__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.l);
+}
+__device__ __forceinline__ int fmod_(int n, const FastDiv& f) { return n - fdiv(n, f) * f.d; }
+
 // One distinct cube shape of a batch, with its line length and FFT factorisation.
 struct Shape {
   int D;
@@ -31,7 +46,19 @@ struct Shape {
   int strides[kMaxD];        // row-major element strides (last dimension fastest)
   int c[kMaxD];              // L / N_d
   int radix[kMaxStages];     // radices, product = L
+  int tstep[kMaxStages];     // L / (Ns R): twiddle stride of each stage
+  FastDiv fdims[kMaxD];      // division by N_d
+  FastDiv fL;                // division by L
+  FastDiv fnb[kMaxStages];   // division by L / R of each stage
+  FastDiv fns[kMaxStages];   // division by Ns (product of the earlier radices) of each stage
 };
+
+// [c_d v]_L in [0, L) for any int v: v is first reduced into [0, N_d) (schedule entries are never
+// trusted to be in range), then c_d v < L N_d < 2^31 (a plan invariant) is reduced by L.
+__device__ __forceinline__ int cmodL(const Shape& sh, int d, int v) {
+  const int vr = fmod_(v & 0x3fffffff, sh.fdims[d]);
+  return fmod_(sh.c[d] * vr, sh.fL);
+}
 
 // True when every component lies on the grid (0 <= k_d < N_d); entries that fail are skipped by
 // every kernel that reads caller-supplied frequencies.
@@ -41,12 +68,6 @@ __device__ __forceinline__ bool on_grid(const Shape& sh, const int* k) {
 #pragma unroll
   for (int d = 0; d < D; ++d) ok = ok && k[d] >= 0 && k[d] < sh.dims[d];
   return ok;
-}
-
-// [c_d v]_L in [0, L) for any int v (schedule entries are reduced, never trusted to be in range).
-__device__ __forceinline__ int cmod(int c, int v, int L) {
-  long long r = ((long long)c * (long long)v) % L;
-  return (int)(r < 0 ? r + L : r);
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -66,32 +87,83 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 // buf[j * L + l] = x(n_j(l)),  n_d(l) = [alpha_d l + tau_d]_{N_d},  line d+1 adds e_d (mod N_d).
 // One thread owns one l and issues the D+1 loads of that l back to back; line D (offset on the
 // fastest dimension) is the neighbour of line 0 in memory and usually shares its 32-byte sector.
-template <int D>
+// Global loads of one sample: LM = 0 through L1 (read-only path, ld.global.nc), LM = 1 cached in
+// L2 only (ld.global.cg).
+template <int LM>
+__device__ __forceinline__ float2 load_sample(const float2* p) {
+  if (LM == 1) return __ldcg(p);
+  return __ldg(p);
+}
+
+template <int D, int LM = 0>
 __device__ __forceinline__ void gather_lines(float2* __restrict__ buf, const float2* __restrict__ x,
                                              const Shape& sh, const int* __restrict__ alpha,
                                              const int* __restrict__ tau) {
   const int L = sh.L;
   int al[D], ta[D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) { al[d] = __ldg(alpha + d); ta[d] = __ldg(tau + d); }
+  for (int d = 0; d < D; ++d) {
+    al[d] = fmod_(__ldg(alpha + d) & 0x3fffffff, sh.fdims[d]);
+    ta[d] = fmod_(__ldg(tau + d) & 0x3fffffff, sh.fdims[d]);
+  }
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
     int n[D];
     int base = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      n[d] = (int)(((unsigned)al[d] * (unsigned)l + (unsigned)ta[d]) % (unsigned)sh.dims[d]);
+      n[d] = fmod_(al[d] * l + ta[d], sh.fdims[d]);
       base += n[d] * sh.strides[d];
     }
     float2 v[D + 1];
-    v[0] = __ldg(x + base);
+    v[0] = load_sample<LM>(x + base);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int step = (n[d] + 1 == sh.dims[d]) ? -(sh.dims[d] - 1) * sh.strides[d] : sh.strides[d];
-      v[d + 1] = __ldg(x + base + step);
+      v[d + 1] = load_sample<LM>(x + base + step);
     }
 #pragma unroll
     for (int j = 0; j <= D; ++j) buf[j * L + l] = v[j];
   }
+}
+
+// Asynchronous variant (cp.async, 8 bytes per sample, through L1): the copies land in shared
+// memory after the issuing thread's cp.async.wait_group and a CTA barrier.  Lets the gather of
+// iteration t+1 (whose slope and offset are known in advance) overlap iteration t's compute.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int D>
+__device__ __forceinline__ void gather_lines_async(float2* __restrict__ buf, const float2* __restrict__ x,
+                                                   const Shape& sh, const int* __restrict__ alpha,
+                                                   const int* __restrict__ tau) {
+  const int L = sh.L;
+  int al[D], ta[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    al[d] = fmod_(__ldg(alpha + d) & 0x3fffffff, sh.fdims[d]);
+    ta[d] = fmod_(__ldg(tau + d) & 0x3fffffff, sh.fdims[d]);
+  }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    int n[D];
+    int base = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      n[d] = fmod_(al[d] * l + ta[d], sh.fdims[d]);
+      base += n[d] * sh.strides[d];
+    }
+    cp_async8(buf + l, x + base);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int step = (n[d] + 1 == sh.dims[d]) ? -(sh.dims[d] - 1) * sh.strides[d] : sh.strides[d];
+      cp_async8(buf + (d + 1) * L + l, x + base + step);
+    }
+  }
+  cp_async_commit();
 }
 
 // Grid-point address of line j at position l (used by the projection adjoint's scatter).
@@ -100,7 +172,7 @@ __device__ __forceinline__ int line_address(const Shape& sh, const int* al, cons
   int base = 0;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    int nd = (int)(((unsigned)al[d] * (unsigned)l + (unsigned)ta[d] + (unsigned)(j == d + 1)) % (unsigned)sh.dims[d]);
+    const int nd = fmod_(al[d] * l + ta[d] + (j == d + 1 ? 1 : 0), sh.fdims[d]);
     base += nd * sh.strides[d];
   }
   return base;
@@ -185,16 +257,16 @@ __device__ __forceinline__ void butterfly<8>(float2 (&v)[8]) {
 
 template <int R>
 __device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2* __restrict__ out, int L,
-                                          int nlines, int Ns, const float2* __restrict__ tw, float sc) {
-  const int nb = L / R;
-  const int tstep = L / (Ns * R);
+                                          int nlines, int Ns, int tstep, const FastDiv& fnb, const FastDiv& fns,
+                                          const float2* __restrict__ tw, float sc) {
+  const int nb = fnb.d;
   const int total = nlines * nb;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int line = w / nb;
+    const int line = fdiv(w, fnb);
     const int j = w - line * nb;
     const float2* src = in + line * L;
     float2* dst = out + line * L;
-    const int k = j % Ns;
+    const int k = fmod_(j, fns);
     float2 v[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) v[i] = src[j + i * nb];
@@ -212,25 +284,27 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2*
 // Any radix (used for prime factors other than 2, 3, 5): O(R^2) per butterfly, inputs re-read
 // from shared memory.
 __device__ __forceinline__ void fft_stage_generic(const float2* __restrict__ in, float2* __restrict__ out,
-                                                  int L, int nlines, int Ns, int R,
-                                                  const float2* __restrict__ tw, float sc) {
-  const int nb = L / R;
-  const int tstep = L / (Ns * R);
-  const int rstep = L / R;           // exp(-j 2 pi x / R) = tw[(x mod R) * L / R]
+                                                  int L, int nlines, int Ns, int R, int tstep, const FastDiv& fnb,
+                                                  const FastDiv& fns, const float2* __restrict__ tw, float sc) {
+  const int nb = fnb.d;
+  const int rstep = nb;              // exp(-j 2 pi x / R) = tw[(x mod R) * L / R]
   const int total = nlines * nb;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int line = w / nb;
+    const int line = fdiv(w, fnb);
     const int j = w - line * nb;
     const float2* src = in + line * L;
     float2* dst = out + line * L;
-    const int k = j % Ns;
+    const int k = fmod_(j, fns);
     const int base = (j - k) * R + k;
     for (int q = 0; q < R; ++q) {
       float2 acc = make_float2(0.f, 0.f);
+      int x = 0;                     // (i q) mod R, advanced incrementally
       for (int i = 0; i < R; ++i) {
         float2 v = src[j + i * nb];
         if (k != 0 && i != 0) v = cmul(v, tw[i * k * tstep]);
-        acc = cadd(acc, cmul(v, tw[((i * q) % R) * rstep]));
+        acc = cadd(acc, cmul(v, tw[x * rstep]));
+        x += q;
+        if (x >= R) x -= R;
       }
       dst[base + q * Ns] = cscale(acc, sc);
     }
@@ -248,14 +322,15 @@ __device__ __forceinline__ float2* fft_lines(float2* buf0, float2* buf1, int nli
   const int L = sh.L;
   for (int s = 0; s < sh.nst; ++s) {
     const int R = sh.radix[s];
+    const int ts = sh.tstep[s];
     const float sc = (s == sh.nst - 1) ? scale : 1.f;
     switch (R) {
-      case 2: fft_stage<2>(in, out, L, nlines, Ns, tw, sc); break;
-      case 3: fft_stage<3>(in, out, L, nlines, Ns, tw, sc); break;
-      case 4: fft_stage<4>(in, out, L, nlines, Ns, tw, sc); break;
-      case 5: fft_stage<5>(in, out, L, nlines, Ns, tw, sc); break;
-      case 8: fft_stage<8>(in, out, L, nlines, Ns, tw, sc); break;
-      default: fft_stage_generic(in, out, L, nlines, Ns, R, tw, sc); break;
+      case 2: fft_stage<2>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
+      case 3: fft_stage<3>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
+      case 4: fft_stage<4>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
+      case 5: fft_stage<5>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
+      case 8: fft_stage<8>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
+      default: fft_stage_generic(in, out, L, nlines, Ns, R, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
     }
     __syncthreads();
     float2* t = in;
@@ -334,8 +409,8 @@ __device__ __forceinline__ void project_entry(float2* bins, int line_stride, con
     msum += ca[d] * k[d];
     psum += ct[d] * k[d];
   }
-  const int m = msum % L;
-  const int p = psum % L;
+  const int m = fmod_(msum, sh.fL);
+  const int p = fmod_(psum, sh.fL);
   float2 v = cmulc(a, tw[p]);
   atomicAdd(&bins[m].x, sign * v.x);
   atomicAdd(&bins[m].y, sign * v.y);
@@ -388,7 +463,6 @@ template <int D>
 __device__ __forceinline__ int classify_fp32(const float2 s0, const float2* sd, const Shape& sh,
                                              const Thresholds& th, int* k, bool* t0_counted) {
   const float kInvTwoPi = 0.159154943091895336f;
-  const float kPiGuard = 3.14158f;                 // |phi| closer to pi than this: wrap side uncertain
   const float e0 = fmaf(s0.x, s0.x, s0.y * s0.y);
   if (e0 < th.t0_lo) return kReject;               // T0 fails
   if (!(e0 > th.t0_hi)) return kUndecided;
@@ -405,8 +479,10 @@ __device__ __forceinline__ int classify_fp32(const float2 s0, const float2* sd, 
   for (int d = 0; d < D; ++d) {                    // decode + T2
     const float re = fmaf(sd[d].x, s0.x, sd[d].y * s0.y);
     const float im = fmaf(sd[d].y, s0.x, -(sd[d].x * s0.y));
+    // FP32 and FP64 may put phi on opposite sides of +-pi; u then differs by N_d, which moves
+    // floor(u + 1/2) by N_d and leaves both k_d mod N_d and the distance to the grid unchanged,
+    // so the certification below holds modulo N_d.
     const float phi = atan2f(im, re);
-    if (fabsf(phi) > kPiGuard) return kUndecided;
     const float nd = (float)sh.dims[d];
     const float u = nd * phi * kInvTwoPi;
     const float r = floorf(u + 0.5f);
@@ -414,8 +490,9 @@ __device__ __forceinline__ int classify_fp32(const float2 s0, const float2* sd, 
     const float band = 2e-6f * nd + 1e-6f;
     if (fabsf(dist - th.eta_f) <= band || fabsf(dist - 0.5f) <= band) return kUndecided;
     if (dist > th.eta_f) return kReject;
-    int kd = (int)r % sh.dims[d];
+    int kd = (int)r;                               // r in [-N_d/2, N_d/2 + 1]
     if (kd < 0) kd += sh.dims[d];
+    if (kd >= sh.dims[d]) kd -= sh.dims[d];
     k[d] = kd;
   }
   return kAccept;
@@ -444,8 +521,9 @@ __device__ __forceinline__ int classify_fp64(const float2 s0, const float2* sd, 
     const double u = (double)sh.dims[d] * atan2(im, re) / kTwoPi;
     const double r = floor(u + 0.5);
     if (fabs(u - r) > th.eta) ok = false;                             // T2
-    int kd = (int)r % sh.dims[d];
+    int kd = (int)r;                                                  // r in [-N_d/2, N_d/2 + 1]
     if (kd < 0) kd += sh.dims[d];
+    if (kd >= sh.dims[d]) kd -= sh.dims[d];
     k[d] = kd;
   }
   return ok ? kAccept : kReject;
@@ -483,8 +561,8 @@ __device__ __forceinline__ void decode_bins(const float2* bins, int line_stride,
       psum += ct[d] * k[d];
       key += k[d] * sh.strides[d];
     }
-    if (msum % L != m) continue;                                      // T3
-    const float2 a = cmul(s0, tw[psum % L]);                          // a = s_0 W^-p
+    if (fmod_(msum, sh.fL) != m) continue;                            // T3
+    const float2 a = cmul(s0, tw[fmod_(psum, sh.fL)]);                // a = s_0 W^-p
     if (!set_insert<D>(s, k, key, a)) my_ovf = true;
   }
   if (my_t0) atomicAdd(t0, my_t0);
