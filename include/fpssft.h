@@ -194,6 +194,36 @@ fpssft_status fpssft_adjoint(fpssft_plan_t plan, fpssft_adj_mode mode, const voi
                              int n_sched, const int32_t* k, const int32_t* count, void* grad_out,
                              void* stream);
 
+/* Size of the fixed device scratch used by fpssft_recover_noalloc (bytes). */
+#define FPSSFT_NOALLOC_SCRATCH_BYTES (1 << 20)
+
+/* fpssft_recover without any device allocation (no counterpart in the paper: this is about how
+ * the library obtains memory, not about the method).  For callers that cannot allocate device
+ * memory when they recover -- code that runs under a memory pool or arena owned by someone else,
+ * inside regions where cudaMalloc is forbidden or would synchronise, or within a fixed memory
+ * budget.  No plan is needed: the tables a plan would allocate (shapes, per-signal iteration
+ * budgets, work order, twiddles) and the work counter are placed in one file-scope device array
+ * of FPSSFT_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds until the process
+ * exits.  The call allocates nothing on the device and calls no allocating CUDA or library routine.
+ *   D, batch, dims (HOST int64 [batch][D]), params: as for fpssft_plan_create.
+ *   cubes, offsets, alpha, tau, init_count, out_*: as for fpssft_recover, on the device; alpha and
+ *     tau are [batch][T_max][D] with T_max = params->T when T > 0, else the largest per-signal
+ *     budget floor(N_b / ((D+1) L_b)).
+ * Limits: the tables must fit the array -- about 12 bytes per signal plus one 8-byte twiddle per
+ * line position of every distinct line length, and at most 64 distinct shapes; larger requests
+ * return FPSSFT_ERR_UNSUPPORTED with a message and launch nothing.
+ * The first call on a device also looks up the array's device address and raises the recovery
+ * kernel's shared-memory limit; make that first call before any stream capture.  The call copies
+ * the tables into the array and clears the work counter on `stream` before the launch.
+ * Every call shares the one array and it keeps the last call's contents, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race: issue them one after
+ * another on one stream. */
+fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t* dims, const fpssft_params* params,
+                                     const void* cubes, const int64_t* offsets, const int32_t* alpha,
+                                     const int32_t* tau, const int32_t* init_count, int32_t* out_k,
+                                     void* out_a, int32_t* out_count, int32_t* out_iters,
+                                     int32_t* out_status, void* stream);
+
 /* Measurement helper (no counterpart in the paper): the random-gather ceiling the line gather is
  * compared against.  threads_total threads each read reads_per_thread 8-byte elements at
  * pseudo-random positions of buf (device, n_elems complex64 elements, a power of two; use a

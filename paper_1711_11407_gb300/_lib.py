@@ -98,6 +98,7 @@ SIGNATURES = {
     "fpssft_adjoint": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
     "fpssft_probe_gather": (_I, [_P, ctypes.c_int64, _I, _I, _I, _I, _P, _P]),
     "fpssft_l2_fetch_granularity": (_I, [_I, ctypes.POINTER(ctypes.c_int)]),
+    "fpssft_recover_noalloc": (_I, [_I, _I, _P, ctypes.POINTER(CParams), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fpssft_last_error": (ctypes.c_char_p, []),
     "fpssft_version": (ctypes.c_char_p, []),
 }

@@ -46,18 +46,34 @@ constexpr int kStatusCapacity = FPSSFT_ERR_CAPACITY;
 
 // The dynamic shared-memory limit is a property of the kernel (per device), shared by every plan:
 // raise it when a plan needs more, never lower it under a plan that needs more.
+// (fixed-size table: recording a limit allocates nothing)
+struct AttrEntry {
+  int dev;
+  const void* func;
+  int bytes;
+};
 std::mutex g_attr_mutex;
-std::map<std::pair<int, const void*>, int> g_attr_bytes;
+AttrEntry g_attr_tab[1024];
+int g_attr_n = 0;
 
 cudaError_t ensure_dynamic_smem(const void* func, size_t bytes) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_attr_mutex);
-  int& cur = g_attr_bytes[{dev, func}];
-  if ((int)bytes <= cur) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) cur = (int)bytes;
-  return e;
+  AttrEntry* e = nullptr;
+  for (int i = 0; i < g_attr_n && !e; ++i)
+    if (g_attr_tab[i].dev == dev && g_attr_tab[i].func == func) e = &g_attr_tab[i];
+  if (!e) {
+    if (g_attr_n >= 1024) return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = &g_attr_tab[g_attr_n++];
+    e->dev = dev;
+    e->func = func;
+    e->bytes = 0;
+  }
+  if ((int)bytes <= e->bytes) return cudaSuccess;
+  const cudaError_t r = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (r == cudaSuccess) e->bytes = (int)bytes;
+  return r;
 }
 
 struct DeviceTables {
@@ -1328,3 +1344,240 @@ extern "C" fpssft_status fpssft_l2_fetch_granularity(int bytes, int* previous) {
 extern "C" const char* fpssft_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* fpssft_version(void) { return "fpssft-gb300 0.1 (sm_103a)"; }
+
+// ================================================================================================
+// Recovery without any device allocation
+// ================================================================================================
+// Some callers cannot allocate device memory at the time they recover: code running under a
+// memory pool or arena owned by someone else, inside a region where cudaMalloc is forbidden or
+// would synchronise, or with a fixed device-memory budget.  fpssft_recover_noalloc serves them:
+// the plan's tables (shapes, per-signal budgets, work order, twiddles) and the work counter live in
+// one file-scope device array of fixed size instead of plan-owned allocations.
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)FPSSFT_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxShapes = 64;
+constexpr int kNoallocMaxDevices = 64;
+
+// The device copy of the tables.  Every GPU that loads the library holds these bytes until the
+// process exits.  In host code the name is only a stand-in: kernels receive the device address
+// obtained by cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Host-side staging of the tables (static: building them allocates nothing).
+alignas(256) unsigned char g_noalloc_host[kNoallocScratchBytes];
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_dev[kNoallocMaxDevices] = {};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int factorize_into(int L, int* out) {
+  int n = L, k = 0;
+  const int small[] = {8, 4, 2, 3, 5};
+  for (int f : small)
+    while (n % f == 0 && k < kMaxStages) { out[k++] = f; n /= f; }
+  for (int f = 7; (long long)f * f <= n && k < kMaxStages; f += 2)
+    while (n % f == 0 && k < kMaxStages) { out[k++] = f; n /= f; }
+  if (n > 1) {
+    if (k >= kMaxStages) return -1;
+    out[k++] = n;
+  }
+  return k;
+}
+
+}  // namespace
+
+extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t* dims, const fpssft_params* params,
+                                                const void* cubes, const int64_t* offsets, const int32_t* alpha,
+                                                const int32_t* tau, const int32_t* init_count, int32_t* out_k,
+                                                void* out_a, int32_t* out_count, int32_t* out_iters,
+                                                int32_t* out_status, void* stream) {
+  if (params == nullptr) return fail(FPSSFT_ERR_INVALID, "null params");
+  if (D < 1 || D > kMaxD) return fail(FPSSFT_ERR_INVALID, "D must be in [1, 4]");
+  if (batch < 0) return fail(FPSSFT_ERR_INVALID, "batch must be >= 0");
+  if (batch == 0) return FPSSFT_OK;
+  if (!dims || !cubes || !offsets || !alpha || !tau || !out_k || !out_a || !out_count || !out_iters || !out_status)
+    return fail(FPSSFT_ERR_INVALID, "null pointer");
+  const fpssft_params& pr = *params;
+  if (pr.k_cap < 1 || pr.k_cap > (1 << 22)) return fail(FPSSFT_ERR_INVALID, "k_cap must be in [1, 2^22]");
+  if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
+  if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
+  if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
+  if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
+  if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
+
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  int dev = 0;
+  FPSSFT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(FPSSFT_ERR_UNSUPPORTED, "device index out of range");
+  // set-up, once per device, with that device current: the device address of the scratch array
+  if (g_noalloc_dev[dev] == nullptr) {
+    void* ptr = nullptr;
+    FPSSFT_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_dev[dev] = static_cast<unsigned char*>(ptr);
+  }
+  unsigned char* dscratch = g_noalloc_dev[dev];
+
+  // ---- tables, built in the static host staging area (same rules as fpssft_plan_create) --------
+  const size_t off_counter = 0;
+  const size_t off_shapes = 256;
+  const size_t off_sig_shape = align256(off_shapes + kNoallocMaxShapes * sizeof(Shape));
+  const size_t off_sig_T = align256(off_sig_shape + (size_t)batch * sizeof(int));
+  const size_t off_order = align256(off_sig_T + (size_t)batch * sizeof(int));
+  const size_t off_tw = align256(off_order + (size_t)batch * sizeof(int));
+  if (off_tw > kNoallocScratchBytes)
+    return fail(FPSSFT_ERR_UNSUPPORTED, "batch exceeds the fixed scratch of fpssft_recover_noalloc (FPSSFT_NOALLOC_SCRATCH_BYTES)");
+  Shape* shapes = reinterpret_cast<Shape*>(g_noalloc_host + off_shapes);
+  int* sig_shape = reinterpret_cast<int*>(g_noalloc_host + off_sig_shape);
+  int* sig_T = reinterpret_cast<int*>(g_noalloc_host + off_sig_T);
+  int* order = reinterpret_cast<int*>(g_noalloc_host + off_order);
+  float2* tw = reinterpret_cast<float2*>(g_noalloc_host + off_tw);
+  const size_t tw_cap = (kNoallocScratchBytes - off_tw) / sizeof(float2);
+  int n_shapes = 0, L_max = 1, T_max = 1;
+  size_t tw_used = 0;
+  for (int b = 0; b < batch; ++b) {
+    int dv[kMaxD] = {1, 1, 1, 1};
+    long long N = 1, L = 1, nmax = 1;
+    for (int d = 0; d < D; ++d) {
+      const int64_t n = dims[(size_t)b * D + d];
+      if (n < 1 || n > (1 << 24)) return fail(FPSSFT_ERR_INVALID, "every dimension must be in [1, 2^24]");
+      dv[d] = (int)n;
+      N *= n;
+      L = L / std::gcd(L, (long long)n) * n;
+      nmax = std::max(nmax, (long long)n);
+      if (N > (1LL << 31) - 1 || L > (1LL << 24)) return fail(FPSSFT_ERR_UNSUPPORTED, "cube or line too large (N < 2^31, L <= 2^24)");
+    }
+    if ((long long)D * L * nmax >= (1LL << 31)) return fail(FPSSFT_ERR_UNSUPPORTED, "D * L * max N_d must stay below 2^31");
+    int si = -1;
+    for (int q = 0; q < n_shapes && si < 0; ++q) {
+      bool same = true;
+      for (int d = 0; d < D; ++d) same = same && shapes[q].dims[d] == dv[d];
+      if (same) si = q;
+    }
+    if (si < 0) {
+      if (n_shapes >= kNoallocMaxShapes) return fail(FPSSFT_ERR_UNSUPPORTED, "more than 64 distinct shapes in one batch");
+      Shape& sh = shapes[n_shapes];
+      std::memset(&sh, 0, sizeof(Shape));
+      sh.D = D;
+      sh.L = (int)L;
+      sh.N = (int)N;
+      int stride = 1;
+      for (int d = D - 1; d >= 0; --d) { sh.dims[d] = dv[d]; sh.strides[d] = stride; stride *= dv[d]; }
+      for (int d = 0; d < D; ++d) sh.c[d] = (int)(L / dv[d]);
+      const int nst = factorize_into((int)L, sh.radix);
+      if (nst < 0) return fail(FPSSFT_ERR_UNSUPPORTED, "too many FFT stages");
+      sh.nst = nst;
+      for (int d = 0; d < kMaxD; ++d) sh.fdims[d] = make_fastdiv(d < D ? dv[d] : 1);
+      sh.fL = make_fastdiv((int)L);
+      int ns = 1;
+      for (int s = 0; s < nst; ++s) {
+        sh.tstep[s] = (int)(L / ((long long)ns * sh.radix[s]));
+        sh.fnb[s] = make_fastdiv((int)(L / sh.radix[s]));
+        sh.fns[s] = make_fastdiv(ns);
+        ns *= sh.radix[s];
+      }
+      int reuse = -1;   // twiddle table shared by shapes with the same L
+      for (int q = 0; q < n_shapes && reuse < 0; ++q)
+        if (shapes[q].L == sh.L) reuse = shapes[q].tw_off;
+      if (reuse >= 0) {
+        sh.tw_off = reuse;
+      } else {
+        if (tw_used + (size_t)L > tw_cap)
+          return fail(FPSSFT_ERR_UNSUPPORTED, "twiddle tables exceed the fixed scratch of fpssft_recover_noalloc");
+        sh.tw_off = (int)tw_used;
+        for (long long q = 0; q < L; ++q) {
+          const double ang = 2.0 * M_PI * (double)q / (double)L;
+          tw[tw_used + q] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        }
+        tw_used += (size_t)L;
+      }
+      si = n_shapes++;
+    }
+    sig_shape[b] = si;
+    const long long budget = std::max(1LL, N / ((long long)(D + 1) * L));
+    sig_T[b] = pr.T > 0 ? pr.T : (int)std::min(budget, (long long)1 << 30);
+    L_max = std::max(L_max, (int)L);
+    T_max = std::max(T_max, sig_T[b]);
+    order[b] = b;
+  }
+  std::sort(order, order + batch, [&](int a, int b) {
+    const int La = shapes[sig_shape[a]].L, Lb = shapes[sig_shape[b]].L;
+    if (La != Lb) return La > Lb;
+    if (sig_T[a] != sig_T[b]) return sig_T[a] > sig_T[b];
+    return a < b;
+  });
+  int hb = 1;
+  while ((1 << hb) < 2 * pr.k_cap) ++hb;
+
+  int optin = 0, sms = 1;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (optin <= 0) optin = 227 * 1024;
+  if (sms <= 0) sms = 1;
+  const size_t static_reserve = sizeof(Shape) + 256;
+  const bool want_pf = pr.gather_mode == 0 || pr.gather_mode == 3;
+  bool tw_smem = true, pf = want_pf;
+  SmemLayout lay = recover_layout(D, L_max, pr.k_cap, 1 << hb, true, want_pf);
+  if (lay.total + static_reserve > (size_t)optin) { pf = false; lay = recover_layout(D, L_max, pr.k_cap, 1 << hb, true, false); }
+  if (lay.total + static_reserve > (size_t)optin) { tw_smem = false; lay = recover_layout(D, L_max, pr.k_cap, 1 << hb, false, false); }
+  if (lay.total + static_reserve > (size_t)optin)
+    return fail(FPSSFT_ERR_UNSUPPORTED, "lines + recovered set exceed one CTA's shared memory (L_max or k_cap too large)");
+  int threads = pr.threads;
+  if (threads == 0) {
+    threads = 64;
+    while (threads < L_max && threads < 512) threads <<= 1;
+  }
+
+  // ---- upload the tables and clear the work counter (no allocation: copies into the array) -----
+  const size_t bytes = off_tw + tw_used * sizeof(float2);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FPSSFT_CUDA_TRY(cudaMemcpyAsync(dscratch + off_shapes, g_noalloc_host + off_shapes, bytes - off_shapes,
+                                  cudaMemcpyHostToDevice, s));
+  FPSSFT_CUDA_TRY(cudaMemsetAsync(dscratch + off_counter, 0, sizeof(int), s));
+
+  RecoverArgs A;
+  A.cubes = static_cast<const float2*>(cubes);
+  A.offsets = offsets;
+  A.alpha = alpha;
+  A.tau = tau;
+  A.sched_stride = T_max * D;
+  A.tab = DeviceTables{reinterpret_cast<const Shape*>(dscratch + off_shapes),
+                       reinterpret_cast<const int*>(dscratch + off_sig_shape),
+                       reinterpret_cast<const int*>(dscratch + off_sig_T),
+                       reinterpret_cast<const int*>(dscratch + off_order),
+                       reinterpret_cast<const float2*>(dscratch + off_tw)};
+  A.work_counter = reinterpret_cast<int*>(dscratch + off_counter);
+  A.batch = batch;
+  A.k_cap = pr.k_cap;
+  A.hash_bits = hb;
+  A.L_max = L_max;
+  A.tw_smem = tw_smem ? 1 : 0;
+  A.prefetch = pf ? 1 : 0;
+  A.gather_mode = pr.gather_mode;
+  A.early_stop = pr.early_stop;
+  {
+    fpssft_plan_s tmp;   // only to reuse the threshold derivation
+    tmp.p = pr;
+    A.th = tmp.thresholds();
+  }
+  A.init_count = init_count;
+  A.out_k = out_k;
+  A.out_a = static_cast<float2*>(out_a);
+  A.out_count = out_count;
+  A.out_iters = out_iters;
+  A.out_status = out_status;
+  return dispatch_D(D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    // raise (never lower) the kernel's dynamic shared-memory limit; shared with the plan path
+    FPSSFT_CUDA_TRY(ensure_dynamic_smem((const void*)k_recover<DD>, lay.total));
+    int per_sm = 0;
+    FPSSFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover<DD>, threads, lay.total));
+    if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
+    if (pr.ctas_per_sm > 0) per_sm = std::min(per_sm, pr.ctas_per_sm);
+    const int grid = std::max(1, std::min(batch, per_sm * sms));
+    k_recover<DD><<<grid, threads, lay.total, s>>>(A);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
