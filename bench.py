@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--gather-mode", type=int, default=0)
+    ap.add_argument("--fft-path", type=int, default=0)
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1: leave)")
     return ap.parse_args()
 
@@ -245,7 +246,8 @@ def main():
     if seed is None:
         seed = 1234 + {v: k for k, v in synth.WORKLOAD_IDS.items()}[args.workload] + 1000 * rank
     wl = synth.make_workload(args.workload, seed=seed, batch=args.batch)
-    p = configs.params_for(wl, threads=args.threads, ctas_per_sm=args.ctas_per_sm, gather_mode=args.gather_mode)
+    p = configs.params_for(wl, threads=args.threads, ctas_per_sm=args.ctas_per_sm, gather_mode=args.gather_mode,
+                           fft_path=args.fft_path)
     from paper_1711_11407_gb300.api import l2_fetch_granularity
     l2_prev = l2_fetch_granularity(args.l2_fetch)
     plan = Plan(wl.dims, p)

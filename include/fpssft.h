@@ -76,9 +76,13 @@ typedef struct {
   int fp64_decisions;/* nonzero: evaluate T0..T2 in FP64 for every bin.  0 (default): evaluate in
                         FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a
                         guard band around a threshold -- the verdicts are the same either way */
-  int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice, 1 = synchronous
-                        through L1, 2 = synchronous cached in L2 only, 3 = asynchronous copies of
-                        the next iteration's lines while the current one computes */
+  int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice (synchronous
+                        through L1), 1 = synchronous through L1, 2 = synchronous cached in L2 only,
+                        3 = asynchronous copies of the next iteration's lines while the current
+                        one computes (needs a third line buffer in shared memory) */
+  int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
+                        shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
+                        FFT (every L of the batch in {32, 64, 128, 256}) */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;
@@ -96,6 +100,7 @@ typedef struct {
   int smem_bytes;     /* dynamic shared memory per recovery CTA */
   int twiddles_in_smem;
   int prefetch;       /* 1: the next iteration's lines are gathered while the current one computes */
+  int fft_path;       /* 1: shared-memory FFT, one CTA per signal; 2: register FFT, one warp per line */
 } fpssft_plan_info;
 
 /* Create a plan for `batch` signals of dimension D with shapes dims (HOST int64 [batch][D],

@@ -28,11 +28,12 @@ class Params:
     ctas_per_sm: int = 0
     fp64_decisions: bool = False
     gather_mode: int = 0
+    fft_path: int = 0
 
     def c(self):
         return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
                             int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
-                            int(bool(self.fp64_decisions)), int(self.gather_mode))
+                            int(bool(self.fp64_decisions)), int(self.gather_mode), int(self.fft_path))
 
 
 @dataclass

@@ -276,6 +276,307 @@ __global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
   }
 }
 
+// ---- warp-per-line variant for L = 32 R (R = 1, 2, 4, 8) ----------------------------------------
+// One CTA of D+1 warps per signal; warp j gathers line j straight into registers and transforms it
+// with warp_fft (no shared-memory staging, no CTA barrier inside the FFT).  Shared memory holds
+// only the bins (bank-swizzled), the twiddles and the bucket set, so several times more signals
+// are resident per SM than with the shared-memory Stockham path.
+struct WLayout {
+  size_t bins, tw, head, la, lk, nxt, total;
+};
+
+static __host__ __device__ WLayout recover_layout_w(int D, int L_max, int k_cap) {
+  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
+  size_t P = 1;
+  while (P < (size_t)k_cap) P <<= 1;
+  const size_t lines = (size_t)(D + 1) * L_max * sizeof(float2);
+  const size_t sortb = 2 * P * sizeof(int);
+  WLayout w{};
+  size_t off = 0;
+  w.bins = off; off = al(off + (lines > sortb ? lines : sortb));
+  w.tw = off; off = al(off + (size_t)L_max * sizeof(float2));
+  w.head = off; off = al(off + (size_t)L_max * sizeof(int));
+  w.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
+  w.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
+  w.nxt = off; off = al(off + (size_t)k_cap * sizeof(int));
+  w.total = off;
+  return w;
+}
+
+template <int D, int R>
+__device__ __forceinline__ void fft_store_w(float2 (&v)[R], float2* bins, const Shape& sh, const float2* tw, int j,
+                                            int lane, float invL) {
+  warp_fft<R>(v, tw, sh.L, lane);
+  const int br = brev5(lane);
+  float2* out = bins + j * sh.L;
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) out[swz(k2 + R * br)] = cscale(v[k2], invL);
+}
+
+// Sanitised slope and offset of schedule row t (every entry reduced into [0, N_d)).
+template <int D>
+__device__ __forceinline__ void sched_row(const Shape& sh, const int* al, const int* ta, int* alr, int* tar) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    alr[d] = fmod_(__ldg(al + d) & 0x3fffffff, sh.fdims[d]);
+    tar[d] = fmod_(__ldg(ta + d) & 0x3fffffff, sh.fdims[d]);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void peel_set_w(float2* bins, const Shape& sh, const BucketSet& s, int count, const int* ca,
+                                           const int* ct, const float2* __restrict__ tw) {
+  const int L = sh.L;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int k[D];
+    int msum = 0, psum = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      k[d] = s.lk[d * s.k_cap + i];
+      msum += ca[d] * k[d];
+      psum += ct[d] * k[d];
+    }
+    const int m = fmod_(msum, sh.fL);
+    const int p = fmod_(psum, sh.fL);
+    s.nxt[i] = atomicExch(&s.head[m], i);
+    const float2 a = s.la[i];
+    const int pm = swz(m);
+    float2 v = cmulc(a, tw[p]);
+    atomicAdd(&bins[pm].x, -v.x);
+    atomicAdd(&bins[pm].y, -v.y);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      int q = p + sh.c[d] * k[d];
+      if (q >= L) q -= L;
+      v = cmulc(a, tw[q]);
+      atomicAdd(&bins[(d + 1) * L + pm].x, -v.x);
+      atomicAdd(&bins[(d + 1) * L + pm].y, -v.y);
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& sh, const BucketSet& s, const int* ca,
+                                              const int* ct, const float2* __restrict__ tw, const Thresholds& th,
+                                              int* t0, int* ovf) {
+  const int L = sh.L;
+  int my_t0 = 0;
+  bool my_ovf = false;
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    const int pm = swz(m);
+    const float2 s0 = bins[pm];
+    float2 sd[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) sd[d] = bins[(d + 1) * L + pm];
+    int k[D];
+    bool counted = false;
+    int v = th.fp64_all ? kUndecided : classify_fp32<D>(s0, sd, sh, th, k, &counted);
+    if (v == kUndecided) {
+      bool c64 = false;
+      v = classify_fp64<D>(s0, sd, sh, th, k, &c64);
+      counted = c64;
+    }
+    my_t0 += counted ? 1 : 0;
+    if (v != kAccept) continue;
+    int msum = 0, psum = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      msum += ca[d] * k[d];
+      psum += ct[d] * k[d];
+    }
+    if (fmod_(msum, sh.fL) != m) continue;                            // T3
+    const float2 a = cmul(s0, tw[fmod_(psum, sh.fL)]);                // a = s_0 W^-p
+    if (!bucket_insert<D>(s, m, k, a)) my_ovf = true;
+  }
+  if (my_t0) atomicAdd(t0, my_t0);
+  if (my_ovf) atomicOr(ovf, 1);
+}
+
+template <int D>
+__device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh, int count, const Thresholds& th,
+                                            int* skey, int* sidx, int* n_out) {
+  if (threadIdx.x == 0) *n_out = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    if (keep_amplitude(s.la[i], th)) {
+      int key = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) key += s.lk[d * s.k_cap + i] * sh.strides[d];
+      const int pos = atomicAdd(n_out, 1);
+      skey[pos] = key;
+      sidx[pos] = i;
+    }
+  }
+  __syncthreads();
+  const int n = *n_out;
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
+    skey[i] = 0x7fffffff;
+    sidx[i] = -1;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const int ki = skey[i], kj = skey[ixj];
+          if ((ki > kj) == up) {
+            skey[i] = kj;
+            skey[ixj] = ki;
+            const int t = sidx[i];
+            sidx[i] = sidx[ixj];
+            sidx[ixj] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The iterations of one signal on the warp-FFT path.  Warp j owns line j.  The samples of
+// iteration t+1 are loaded into registers right after iteration t's FFT (the schedule is known in
+// advance), so their latency overlaps t's peel and decode.
+template <int D, int R>
+__device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
+                                         const float2* tws, const float2* __restrict__ x, const int* sched_a,
+                                         const int* sched_t, int T, int warp, int lane, float invL, int* s_ca,
+                                         int* s_ct, int* s_t0, int* s_ovf) {
+  const int L = sh.L;
+  float2 nxt[R];
+  if (T > 0) {
+    int alr[D], tar[D];
+    sched_row<D>(sh, sched_a, sched_t, alr, tar);
+    gather_line_regs<D, R>(nxt, x, sh, alr, tar, warp, lane);
+  }
+  int iters = 0;
+  for (int t = 0; t < T; ++t) {
+    const int* al = sched_a + t * D;
+    const int* ta = sched_t + t * D;
+    if (threadIdx.x < D) {
+      const int d = threadIdx.x;
+      s_ca[d] = cmodL(sh, d, al[d]);
+      s_ct[d] = cmodL(sh, d, ta[d]);
+    }
+    for (int m = threadIdx.x; m < L; m += blockDim.x) set.head[m] = -1;
+    float2 v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = nxt[i];
+    fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);
+    if (t + 1 < T) {
+      int alr[D], tar[D];
+      sched_row<D>(sh, al + D, ta + D, alr, tar);
+      gather_line_regs<D, R>(nxt, x, sh, alr, tar, warp, lane);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *s_t0 = 0;
+    peel_set_w<D>(bins, sh, set, min(*set.count, A.k_cap), s_ca, s_ct, tws);
+    __syncthreads();
+    decode_bins_w<D>(bins, sh, set, s_ca, s_ct, tws, A.th, s_t0, s_ovf);
+    __syncthreads();
+    iters = t + 1;
+    const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
+    if (stop) break;
+  }
+  return iters;
+}
+
+#ifndef FPSSFT_W_THREADS_PER_SM
+#define FPSSFT_W_THREADS_PER_SM 640   // resident threads per SM the warp path's register budget targets
+#endif
+
+template <int D>
+__global__ void __launch_bounds__(32 * (D + 1), FPSSFT_W_THREADS_PER_SM / (32 * (D + 1))) k_recover_w(RecoverArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
+  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+  const WLayout lay = recover_layout_w(D, A.L_max, A.k_cap);
+  float2* bins = reinterpret_cast<float2*>(smem + lay.bins);
+  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  BucketSet set;
+  set.lk = reinterpret_cast<int*>(smem + lay.lk);
+  set.la = reinterpret_cast<float2*>(smem + lay.la);
+  set.head = reinterpret_cast<int*>(smem + lay.head);
+  set.nxt = reinterpret_cast<int*>(smem + lay.nxt);
+  set.count = &s_count;
+  set.k_cap = A.k_cap;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+
+  int loaded = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
+    __syncthreads();
+    const int qi = s_sig;
+    if (qi >= A.batch) break;
+    const int b = A.tab.order[qi];
+    const int si = A.tab.sig_shape[b];
+    if (si != loaded) {
+      load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
+      loaded = si;
+    }
+    if (threadIdx.x == 0) {
+      s_count = 0;
+      s_ovf = 0;
+    }
+    __syncthreads();
+    const int L = sh.L;
+    const int R = L >> 5;
+    const float invL = 1.0f / (float)L;
+    const float2* x = A.cubes + A.offsets[b];
+    int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
+    float2* oa_out = A.out_a + (size_t)b * A.k_cap;
+
+    if (A.init_count != nullptr) {   // resume: the caller's set is appended as given
+      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
+      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        int k[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) k[d] = ok_out[i * D + d];
+        if (!on_grid<D>(sh, k)) continue;
+        const int idx = atomicAdd(&s_count, 1);
+#pragma unroll
+        for (int d = 0; d < D; ++d) set.lk[d * A.k_cap + idx] = k[d];
+        set.la[idx] = oa_out[i];
+      }
+      __syncthreads();
+    }
+
+    const int T = A.tab.sig_T[b];
+    const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
+    const int* sched_t = A.tau + (size_t)b * A.sched_stride;
+    int iters = 0;
+    switch (R) {
+      case 1: iters = iterate_w<D, 1>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      case 2: iters = iterate_w<D, 2>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      case 4: iters = iterate_w<D, 4>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      default: iters = iterate_w<D, 8>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+    }
+
+    const int count = min(s_count, A.k_cap);
+    int* skey = reinterpret_cast<int*>(bins);
+    int* sidx = skey + (lay.tw - lay.bins) / (2 * sizeof(int));
+    sort_kept_w<D>(set, sh, count, A.th, skey, sidx, &s_n);
+    const int n = s_n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int i = sidx[r];
+#pragma unroll
+      for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
+      oa_out[r] = set.la[i];
+    }
+    if (threadIdx.x == 0) {
+      A.out_count[b] = n;
+      A.out_iters[b] = iters;
+      A.out_status[b] = s_ovf ? kStatusCapacity : 0;
+    }
+    __syncthreads();
+  }
+}
+
 // ---- projection / raw lines: one CTA per (signal, schedule row) --------------------------------
 struct ProjectArgs {
   const float2* cubes;
@@ -645,6 +946,7 @@ struct fpssft_plan_s {
   int sm_count = 1;
   bool tw_smem = true;
   bool prefetch = true;
+  bool warp_path = false;   // k_recover_w (register FFT per line) instead of k_recover
   size_t smem = 0;
   size_t total_elems = 0;   // sum of N_b (for host staging)
   std::vector<Shape> shapes;
@@ -772,6 +1074,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
   if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
+  if (pr.fft_path < 0 || pr.fft_path > 2) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 2]");
   if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
 
   auto* P = new (std::nothrow) fpssft_plan_s();
@@ -872,9 +1175,33 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (sms <= 0) sms = 1;
   P->sm_count = sms;
   const size_t static_reserve = sizeof(Shape) + 256;
+  // the register-FFT path applies when every line length is 32 R with R in {1, 2, 4, 8}
+  bool warp_ok = true;
+  for (const Shape& sh : P->shapes) {
+    const int R = sh.L / 32;
+    warp_ok = warp_ok && sh.L % 32 == 0 && (R == 1 || R == 2 || R == 4 || R == 8);
+  }
+  warp_ok = warp_ok && pr.k_cap < (1 << 20) && pr.gather_mode != 3;
+  if (pr.fft_path == 2 && !warp_ok) {
+    delete P;
+    return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 2 needs every line length in {32, 64, 128, 256} and no prefetch");
+  }
+  if ((pr.fft_path == 2 || (pr.fft_path == 0 && warp_ok)) && batch > 0) {
+    const WLayout wl = recover_layout_w(D, P->L_max, pr.k_cap);
+    if (wl.total + sizeof(Shape) + 256 <= (size_t)optin) {
+      P->warp_path = true;
+      P->smem = wl.total;
+      P->tw_smem = true;
+      P->prefetch = false;
+      P->threads = 32 * (D + 1);
+    } else if (pr.fft_path == 2) {
+      delete P;
+      return fail(FPSSFT_ERR_UNSUPPORTED, "lines + recovered set exceed one CTA's shared memory (k_cap too large)");
+    }
+  }
   // prefer prefetched gathers (unless a synchronous gather mode is requested) and twiddles in
   // shared memory; drop them in that order if they do not fit
-  const bool want_pf = pr.gather_mode == 0 || pr.gather_mode == 3;
+  const bool want_pf = pr.gather_mode == 3;
   SmemLayout lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, want_pf);
   P->tw_smem = true;
   P->prefetch = want_pf;
@@ -886,17 +1213,19 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false, false);
     P->tw_smem = false;
   }
-  if (lay.total + static_reserve > (size_t)optin) {
+  if (!P->warp_path && lay.total + static_reserve > (size_t)optin) {
     delete P;
     return fail(FPSSFT_ERR_UNSUPPORTED, "lines + recovered set exceed one CTA's shared memory (L_max or k_cap too large)");
   }
-  P->smem = lay.total;
-  if (pr.threads > 0) {
-    P->threads = pr.threads;
-  } else {
-    int t = 64;
-    while (t < P->L_max && t < 512) t <<= 1;
-    P->threads = t;
+  if (!P->warp_path) {
+    P->smem = lay.total;
+    if (pr.threads > 0) {
+      P->threads = pr.threads;
+    } else {
+      int t = 64;
+      while (t < P->L_max && t < 512) t <<= 1;
+      P->threads = t;
+    }
   }
 
   // device workspace
@@ -925,10 +1254,11 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   // kernel attributes and the persistent grid
   fpssft_status st = dispatch_D(D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
-    cudaError_t e2 = ensure_dynamic_smem((const void*)k_recover<DD>, P->smem);
-    if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(k_recover): ") + cudaGetErrorString(e2));
+    const void* kfn = P->warp_path ? (const void*)k_recover_w<DD> : (const void*)k_recover<DD>;
+    cudaError_t e2 = ensure_dynamic_smem(kfn, P->smem);
+    if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
     int per_sm = 0;
-    e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover<DD>, P->threads, P->smem);
+    e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, P->threads, P->smem);
     if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e2));
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
@@ -979,6 +1309,7 @@ extern "C" fpssft_status fpssft_plan_get_info(fpssft_plan_t P, fpssft_plan_info*
   info->smem_bytes = (int)P->smem;
   info->twiddles_in_smem = P->tw_smem ? 1 : 0;
   info->prefetch = P->prefetch ? 1 : 0;
+  info->fft_path = P->warp_path ? 2 : 1;
   return FPSSFT_OK;
 }
 
@@ -1075,7 +1406,10 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   FPSSFT_CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
   return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
-    k_recover<DD><<<P->grid, P->threads, P->smem, s>>>(A);
+    if (P->warp_path)
+      k_recover_w<DD><<<P->grid, P->threads, P->smem, s>>>(A);
+    else
+      k_recover<DD><<<P->grid, P->threads, P->smem, s>>>(A);
     FPSSFT_CUDA_TRY(cudaGetLastError());
     return FPSSFT_OK;
   });
@@ -1516,7 +1850,7 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
   if (optin <= 0) optin = 227 * 1024;
   if (sms <= 0) sms = 1;
   const size_t static_reserve = sizeof(Shape) + 256;
-  const bool want_pf = pr.gather_mode == 0 || pr.gather_mode == 3;
+  const bool want_pf = pr.gather_mode == 3;
   bool tw_smem = true, pf = want_pf;
   SmemLayout lay = recover_layout(D, L_max, pr.k_cap, 1 << hb, true, want_pf);
   if (lay.total + static_reserve > (size_t)optin) { pf = false; lay = recover_layout(D, L_max, pr.k_cap, 1 << hb, true, false); }

@@ -626,3 +626,129 @@ __device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thr
 }
 
 }  // namespace fpssft
+
+namespace fpssft {
+
+// ------------------------------------------------------------------------------------------------
+// Register FFT of one line per warp, for L = 32 R (R = 1, 2, 4, 8, 16)
+// ------------------------------------------------------------------------------------------------
+// Lane l holds v[i] = s(l + 32 i).  With n = l + 32 i and m = k2 + R k1:
+//   s_hat(m) L = sum_l W_32^{l k1} W_L^{l k2} sum_i s(l + 32 i) W_R^{i k2}
+// so each lane takes the R-point DFT of its registers, multiplies register k2 by W_L^{l k2}, and
+// the warp takes a 32-point DFT across lanes for every k2 (radix-2 decimation in frequency with
+// __shfl_xor_sync; the result lands in bit-reversed lane order).  Afterwards lane l holds
+// v[k2] = L s_hat(k2 + R brev5(l)).  tw[q] = exp(-j 2 pi q / L).
+template <int R>
+__device__ __forceinline__ void butterfly_tw(float2 (&v)[R], const float2* __restrict__ tw, int L) {
+  butterfly<R>(v);
+}
+
+template <>
+__device__ __forceinline__ void butterfly_tw<1>(float2 (&v)[1], const float2* __restrict__, int) {}
+
+template <>
+__device__ __forceinline__ void butterfly_tw<16>(float2 (&v)[16], const float2* __restrict__ tw, int L) {
+  // 16 = 4 x 4: DFTs over i2 (stride 4), twiddle W_16^{i1 k2}, DFTs over i1
+  const int q16 = L >> 4;     // W_16^q = tw[q L / 16]
+  float2 a[4][4];
+#pragma unroll
+  for (int i1 = 0; i1 < 4; ++i1) {
+    float2 t[4] = {v[i1], v[i1 + 4], v[i1 + 8], v[i1 + 12]};
+    butterfly<4>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) a[i1][k2] = (i1 * k2 == 0) ? t[k2] : cmul(t[k2], tw[i1 * k2 * q16]);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 t[4] = {a[0][k2], a[1][k2], a[2][k2], a[3][k2]};
+    butterfly<4>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = t[k1];
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void warp_fft(float2 (&v)[R], const float2* __restrict__ tw, int L, int lane) {
+  butterfly_tw<R>(v, tw, L);
+#pragma unroll
+  for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], tw[lane * k2]);
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+    const float2 w = tw[(lane & (h - 1)) * (L / (2 * h))];
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      const float px = __shfl_xor_sync(0xffffffffu, v[k2].x, h);
+      const float py = __shfl_xor_sync(0xffffffffu, v[k2].y, h);
+      if (!upper) {
+        v[k2] = make_float2(v[k2].x + px, v[k2].y + py);
+      } else {
+        v[k2] = cmul(make_float2(px - v[k2].x, py - v[k2].y), w);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
+
+// Bank swizzle of a bin index inside aligned groups of 16 (a bijection on [L] for 16 | L): the
+// bit-reversed stores of warp_fft then spread over all banks.
+__device__ __forceinline__ int swz(int m) { return m ^ ((m >> 4) & 15); }
+
+// Gather line j of iteration (al, ta) into registers: v[i] = x(n_j(lane + 32 i)).
+template <int D, int R>
+__device__ __forceinline__ void gather_line_regs(float2 (&v)[R], const float2* __restrict__ x, const Shape& sh,
+                                                 const int* al, const int* ta, int j, int lane) {
+  int n[D], stepn[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    n[d] = fmod_(al[d] * lane + ta[d] + (j == d + 1 ? 1 : 0), sh.fdims[d]);
+    stepn[d] = fmod_(al[d] * 32, sh.fdims[d]);
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int base = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) base += n[d] * sh.strides[d];
+    v[i] = __ldg(x + base);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      n[d] += stepn[d];
+      if (n[d] >= sh.dims[d]) n[d] -= sh.dims[d];
+    }
+  }
+}
+
+// The recovered set of the warp-FFT kernel: dense list (lk, la) and per-iteration buckets built by
+// the peel (head[m] -> first entry whose bin is m, nxt[i] -> next entry of the same bin).  A
+// frequency decoded from bin m that is already in the set must lie in bucket m (its bin is m by
+// T3), so the buckets replace a hash index.
+struct BucketSet {
+  int* lk;       // [D][k_cap]
+  float2* la;    // [k_cap]
+  int* head;     // [L_max]
+  int* nxt;      // [k_cap]
+  int* count;
+  int k_cap;
+};
+
+template <int D>
+__device__ __forceinline__ bool bucket_insert(const BucketSet& s, int m, const int* k, float2 a) {
+  for (int h = s.head[m]; h >= 0; h = s.nxt[h]) {
+    bool same = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) same = same && s.lk[d * s.k_cap + h] == k[d];
+    if (same) {
+      s.la[h] = cadd(s.la[h], a);
+      return true;
+    }
+  }
+  const int idx = atomicAdd(s.count, 1);
+  if (idx >= s.k_cap) return false;
+#pragma unroll
+  for (int d = 0; d < D; ++d) s.lk[d * s.k_cap + idx] = k[d];
+  s.la[idx] = a;
+  return true;
+}
+
+}  // namespace fpssft

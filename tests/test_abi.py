@@ -32,7 +32,7 @@ def test_library_exports_every_declared_function():
 def _plan(D, batch, dims, **kw):
     lib = _lib.load()
     p = _lib.CParams(kw.get("T", 10), kw.get("k_cap", 64), kw.get("theta0", 1e-3), 1e-3, 0.05, 1,
-                     kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0))
+                     kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0), kw.get("fft_path", 0))
     h = ctypes.c_void_p()
     d = np.ascontiguousarray(np.asarray(dims, np.int64).reshape(-1))
     st = lib.fpssft_plan_create(ctypes.byref(h), D, batch, d.ctypes.data_as(ctypes.c_void_p) if d.size else None,
@@ -52,6 +52,7 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"threads": 1024}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
     (2, 1, [8, 8], {"gather_mode": 4}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"fft_path": 3}, _lib.ERR_INVALID),
     (2, 1, [4096, 3], {}, _lib.ERR_UNSUPPORTED),            # L = 12288 lines exceed one CTA
     (2, 1, [65536, 65536], {}, _lib.ERR_UNSUPPORTED),       # N >= 2^31
 ])

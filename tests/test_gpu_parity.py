@@ -349,3 +349,39 @@ def test_certified_fp32_decisions_equal_fp64_decisions(which):
     assert torch.equal(a.k, b.k)
     # amplitudes carry the rounding of the peel's float atomics, whose order varies between runs
     assert torch.allclose(a.a, b.a, rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("case", ["uneven_2d", "D1_L64", "D3_32cubed", "D2_256", "D4_L32"])
+def test_register_fft_path_equals_shared_memory_path(case):
+    """One warp per line with a register FFT (fft_path 2) against one CTA per signal with the
+    shared-memory mixed-radix FFT (fft_path 1): same sets, counts and iterations; both against the
+    oracle on a few signals."""
+    from paper_1711_11407_gb300.api import Plan
+    if case == "uneven_2d":
+        wl = S.make_workload("uneven_2d", batch=128)
+        T = None
+    else:
+        shapes = {"D1_L64": [(64,)], "D3_32cubed": [(32, 32, 32)], "D2_256": [(256, 128), (16, 256)],
+                  "D4_L32": [(4, 8, 2, 32)]}[case]
+        wl = small_batch(shapes, 8, K=lambda N: max(2, min(40, N // 64)), T=12)
+        T = 12
+    outs = []
+    for path in (1, 2):
+        p = configs.params_for(wl, fft_path=path, k_cap=512)
+        if T is not None:
+            p.T = T
+        plan = Plan(wl.dims, p)
+        assert plan.info["fft_path"] == path
+        outs.append(plan.recover(*to_dev(wl)))
+        torch.cuda.synchronize()
+    a, b = outs
+    assert torch.equal(a.count, b.count) and torch.equal(a.iters, b.iters) and torch.equal(a.status, b.status)
+    for i in range(wl.batch):
+        n = int(a.count[i])
+        assert torch.equal(a.k[i, :n], b.k[i, :n])
+        assert torch.allclose(a.a[i, :n], b.a[i, :n], rtol=AMP_TOL, atol=0)
+    for i in range(min(4, wl.batch)):
+        Ti = int(wl.T[i]) if T is None else T
+        ref = O.recover(wl.cube(i), wl.alpha[i, :Ti], wl.tau[i, :Ti], oracle_params(p, Ti))
+        k, aa = b.signal(i)
+        assert_same_set(k, aa, ref, f"signal {i}")
