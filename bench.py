@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--plain-sample", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="only the timed device loop (for profiler runs)")
+    ap.add_argument("--ceiling", action="store_true", help="with --quick, still measure the gather ceiling")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -320,15 +321,43 @@ def main():
 
     # ---- roofline of the recovery kernel ---------------------------------------------------------
     L = plan.L.astype(np.int64)
-    useful = float(np.sum(iters.astype(np.int64) * (wl.D + 1) * L * 8))           # gathered sample bytes
+    it64 = iters.astype(np.int64)
+    useful = float(np.sum(it64 * (wl.D + 1) * L * 8))           # gathered sample bytes (algorithmic)
     peaks, peak_src = measured_peaks()
     achieved = useful / (ms_per_step / 1000.0) / 1e9
     traffic, _ = profiled_traffic(args.workload, wl.batch)
+    warp_path = plan.info.get("fft_path") == 2
+    kname = f"k_recover_w<{wl.D}>" if warp_path else f"k_recover<{wl.D}>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": achieved / float(peaks["hbm_gbs"]), "traffic": traffic,
-                "peak_source": f"{peak_src} (hbm_gbs, copy bandwidth)",
+                "peak_source": f"{peak_src} (hbm_gbs, copy bandwidth; kernel timed alone: burst figure)",
                 "algorithmic_bytes_per_launch": useful,
-                "kernel": "k_recover<2> (persistent; one CTA per signal; timed per launch with CUDA events)"}
+                "kernel": f"{kname} (persistent; {'one warp per line' if warp_path else 'one CTA per signal'}; "
+                          "one launch per step, CUDA events on the launching stream)"}
+    # second view: the gather against the measured random-access ceiling of this GPU.  Each line
+    # position reads one adjacent pair (lines tau and tau + e_{D-1}) and D - 1 isolated samples.
+    if not args.quick or args.ceiling:
+        from paper_1711_11407_gb300.api import probe_gather
+        probe_buf = torch.zeros(1 << 29, dtype=torch.complex64, device=dev)          # 4 GiB >> L2
+        rates = {}
+        nthr = 152 * 16 * 256
+        for pair in (0, 1):
+            probe_gather(probe_buf, 64, nthr, 0, pair)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                probe_gather(probe_buf, 64, nthr, 0, pair)
+            e1.record()
+            torch.cuda.synchronize()
+            rates[pair] = nthr * 64 / (e0.elapsed_time(e1) / 5 / 1000.0)
+        del probe_buf
+        pairs = float(np.sum(it64 * L))
+        singles = float(np.sum(it64 * L * (wl.D - 1)))
+        t_ceiling = pairs / rates[1] + singles / rates[0]
+        roofline["gather_ceiling"] = {"pair_accesses_per_s": rates[1], "single_accesses_per_s": rates[0],
+                                      "pairs_per_launch": pairs, "singles_per_launch": singles,
+                                      "ceiling_ms": 1000.0 * t_ceiling, "frac": 1000.0 * t_ceiling / ms_per_step,
+                                      "probe": "fpssft_probe_gather, 4 GiB buffer, 9.7M threads x 64 random reads"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -389,7 +418,7 @@ def main():
 
         # ---- FP64 oracle on the host cores (rank 0) --------------------------------------------
         if rank == 0:
-            order = stratified(wl, 256, seed=3)
+            order = stratified(wl, wl.batch, seed=3)
             rate, n, dt = oracle_rate(wl, p, args.cpu_seconds, order)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"{n} signals stratified by shape, {dt:.1f} s single-threaded numpy FP64",
