@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--gather-mode", type=int, default=0)
     ap.add_argument("--fft-path", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch configuration")
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1: leave)")
     return ap.parse_args()
 
@@ -251,11 +252,15 @@ def main():
                            fft_path=args.fft_path)
     from paper_1711_11407_gb300.api import l2_fetch_granularity
     l2_prev = l2_fetch_granularity(args.l2_fetch)
-    plan = Plan(wl.dims, p)
     cubes = torch.from_numpy(wl.cubes).to(dev)
     offs = torch.from_numpy(wl.offsets).to(dev)
     alpha = torch.from_numpy(wl.alpha).to(dev)
     tau = torch.from_numpy(wl.tau).to(dev)
+    tuning = None
+    if not args.no_autotune and args.threads == 0 and args.fft_path == 0 and args.gather_mode == 0:
+        from paper_1711_11407_gb300 import autotune
+        p, tuning = autotune.tune(wl.dims, p, cubes, offs, alpha, tau, reps=3, cache_path=None)
+    plan = Plan(wl.dims, p)
     out = plan.alloc_output(dev)
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -367,7 +372,9 @@ def main():
                        "K": "ceil(N/200)" if args.workload == "uneven_2d" else "per workload",
                        "T": "N/(3L) per signal, early stop", "l2": "256 MiB written between timed steps",
                        "cuda_graph": graph is not None, "parallelism": f"batch sharded over {world} GPU(s), no collective",
-                       "threads": plan.info["threads"], "grid": plan.info["grid"], "smem_bytes": plan.info["smem_bytes"]},
+                       "threads": plan.info["threads"], "grid": plan.info["grid"], "smem_bytes": plan.info["smem_bytes"],
+                       "fft_path": plan.info["fft_path"], "gather_mode": p.gather_mode,
+                       "autotune_ms": tuning},
             "roofline": roofline, "gpu_launches": args.steps, "exact_support_success": success,
             "mean_iterations": float(np.mean(iters)), "clocks": clk.summary()}
 

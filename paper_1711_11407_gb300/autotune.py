@@ -1,0 +1,111 @@
+"""Autotuner for the recovery launch: picks the kernel configuration of fpssft_recover for a batch.
+
+Candidates are the valid combinations of
+  fft_path     1 (one CTA per signal, shared-memory mixed-radix FFT) or 2 (one warp per line,
+               register FFT; only when every line length is 32, 64, 128 or 256),
+  gather_mode  1 (synchronous through L1), 2 (L2 only) or 3 (asynchronous prefetch; path 1 only),
+  threads      CTA size for path 1 (path 2 is fixed at 32 (D+1)).
+Each candidate is timed on the caller's own inputs with CUDA events (warm-up first, a buffer larger
+than L2 written between timed launches); the fastest wins.  Results are cached in a JSON file keyed
+by GPU name, D, the sorted set of shapes, k_cap and T, so a batch with the same layout is not
+re-tuned.  Tuning never changes what is computed, only how it is launched.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from dataclasses import asdict, replace
+
+import numpy as np
+import torch
+
+from ._lib import ERR_UNSUPPORTED, FpssftError
+from .api import Params, Plan
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fpssft_autotune.json")
+
+
+def cache_key(dims, params: Params, gpu_name: str):
+    dims = np.asarray(dims, np.int64)
+    shapes = sorted({tuple(int(v) for v in d) for d in dims})
+    return json.dumps({"gpu": gpu_name, "D": int(dims.shape[1]), "shapes": shapes, "k_cap": int(params.k_cap),
+                       "T": int(params.T)}, sort_keys=True)
+
+
+def candidates(dims, params: Params):
+    """The launch configurations worth timing for this batch (host logic only)."""
+    dims = np.asarray(dims, np.int64)
+    Ls = {math.lcm(*[int(v) for v in d]) for d in dims}
+    warp_ok = all(L % 32 == 0 and L // 32 in (1, 2, 4, 8) for L in Ls)
+    L_max = max(Ls) if Ls else 1
+    out = []
+    if warp_ok:
+        for gm in (1, 2):
+            out.append(replace(params, fft_path=2, gather_mode=gm, threads=0))
+    for th in (128, 256, 512):
+        if th > 4 * max(32, L_max):
+            continue
+        for gm in (1, 3):
+            out.append(replace(params, fft_path=1, gather_mode=gm, threads=th))
+    return out
+
+
+def _time(plan, args, reps, flush):
+    stream = torch.cuda.current_stream()
+    plan.recover(*args)
+    stream.synchronize()
+    total = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.recover(*args)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
+
+
+def tune(dims, params: Params, cubes, offsets, alpha, tau, reps=5, cache_path=DEFAULT_CACHE, use_cache=True):
+    """Return (best Params, {description: ms}) for recovering this batch."""
+    gpu = torch.cuda.get_device_name(cubes.device)
+    key = cache_key(dims, params, gpu)
+    cache = {}
+    if use_cache and cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
+    if use_cache and key in cache:
+        return replace(params, **cache[key]["choice"]), cache[key]["timings"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=cubes.device)
+    timings = {}
+    best, best_ms = None, float("inf")
+    for cand in candidates(dims, params):
+        try:
+            plan = Plan(dims, cand)
+        except FpssftError as e:
+            if e.status == ERR_UNSUPPORTED:
+                continue
+            raise
+        out = plan.alloc_output(cubes.device)
+        ms = _time(plan, (cubes, offsets, alpha, tau, out), reps, flush)
+        desc = f"path={cand.fft_path} gather={cand.gather_mode} threads={plan.info['threads']}"
+        timings[desc] = ms
+        if ms < best_ms:
+            best, best_ms = cand, ms
+        plan.close()
+    if best is None:
+        return params, timings
+    choice = {"fft_path": best.fft_path, "gather_mode": best.gather_mode, "threads": best.threads}
+    if cache_path:
+        cache[key] = {"choice": choice, "timings": timings}
+        try:
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return best, timings

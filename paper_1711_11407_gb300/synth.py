@@ -236,9 +236,14 @@ WORKLOADS = {
                       K=lambda N: -(-N // 200), T=_budget, amp="unit"),
     "images_1024x1024": dict(shapes=[(1024, 1024)], batch=64, K=lambda N: 2000, T=_budget, amp="lognormal",
                              clusters=20, sigma_bins=10.0, snr_db=5.0),
+    # the noisy workloads with the SNR read per sinusoid (sigma^2 = mean |a|^2 / 10^(snr/10))
+    "batched_64x64x64_ps": dict(shapes=[(64, 64, 64)], batch=256, K=lambda N: 500, T=_budget, amp="unit",
+                                snr_db=10.0, snr_mode="per_sinusoid"),
+    "images_1024x1024_ps": dict(shapes=[(1024, 1024)], batch=64, K=lambda N: 2000, T=_budget, amp="lognormal",
+                                clusters=20, sigma_bins=10.0, snr_db=5.0, snr_mode="per_sinusoid"),
 }
 WORKLOAD_IDS = {1: "single_128x128", 2: "single_240x256", 3: "batched_64x64x64", 4: "uneven_2d",
-                5: "images_1024x1024"}
+                5: "images_1024x1024", 13: "batched_64x64x64_ps", 15: "images_1024x1024_ps"}
 
 
 def make_workload(name, seed=None, batch=None, *, shapes=None, K=None, T=None, snr_db="default",
@@ -271,7 +276,7 @@ def make_workload(name, seed=None, batch=None, *, shapes=None, K=None, T=None, s
         Ki = int(Kf(N)) if callable(Kf) else int(Kf)
         k, a, x, sg, al, ta = make_signal(children[i], dims, Ki, Ts[j], clusters=spec.get("clusters", 0),
                                           sigma_bins=spec.get("sigma_bins", 0.0), amp=spec["amp"],
-                                          snr_db=snr, policy=policy)
+                                          snr_db=snr, snr_mode=spec.get("snr_mode", "total"), policy=policy)
         alpha[j, :Ts[j]] = al
         tau[j, :Ts[j]] = ta
         pieces.append(x.reshape(-1).astype(np.complex64))

@@ -1,0 +1,25 @@
+"""Autotuner host logic (no GPU): candidate launch configurations and the cache key."""
+import numpy as np
+
+from paper_1711_11407_gb300 import autotune
+from paper_1711_11407_gb300.api import Params
+
+
+def test_candidates_offer_the_register_path_only_for_eligible_line_lengths():
+    p = Params(T=0, k_cap=512)
+    c = autotune.candidates(np.array([[64, 64], [128, 256], [256, 256]]), p)
+    assert any(x.fft_path == 2 for x in c) and any(x.fft_path == 1 for x in c)
+    c = autotune.candidates(np.array([[240, 256]]), p)          # L = 3840
+    assert all(x.fft_path == 1 for x in c)
+    assert all(x.gather_mode in (1, 2, 3) for x in c)
+    c = autotune.candidates(np.array([[512, 512]]), p)          # L = 512: shared-memory path only
+    assert all(x.fft_path == 1 for x in c)
+
+
+def test_cache_key_ignores_batch_order_and_size():
+    p = Params(T=0, k_cap=512)
+    a = autotune.cache_key(np.array([[64, 64], [128, 128]]), p, "GB300")
+    b = autotune.cache_key(np.array([[128, 128], [64, 64], [64, 64]]), p, "GB300")
+    assert a == b
+    assert a != autotune.cache_key(np.array([[64, 64]]), p, "GB300")
+    assert a != autotune.cache_key(np.array([[64, 64], [128, 128]]), Params(T=0, k_cap=256), "GB300")

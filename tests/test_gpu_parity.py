@@ -385,3 +385,20 @@ def test_register_fft_path_equals_shared_memory_path(case):
         ref = O.recover(wl.cube(i), wl.alpha[i, :Ti], wl.tau[i, :Ti], oracle_params(p, Ti))
         k, aa = b.signal(i)
         assert_same_set(k, aa, ref, f"signal {i}")
+
+
+def test_autotuned_launch_computes_the_same_sets():
+    from paper_1711_11407_gb300 import autotune
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=256)
+    p = configs.params_for(wl)
+    t = to_dev(wl)
+    best, timings = autotune.tune(wl.dims, p, *t, reps=2, cache_path=None)
+    assert len(timings) >= 2
+    ref = Plan(wl.dims, p).recover(*t)
+    got = Plan(wl.dims, best).recover(*t)
+    torch.cuda.synchronize()
+    assert torch.equal(ref.count, got.count) and torch.equal(ref.iters, got.iters)
+    for b in range(wl.batch):
+        n = int(ref.count[b])
+        assert torch.equal(ref.k[b, :n], got.k[b, :n])
