@@ -71,7 +71,8 @@ typedef struct {
   float eta;         /* T2 distance of the decoded phase from the frequency grid */
   int early_stop;    /* nonzero: stop a signal when no bin of line 0 passes T0 after peeling */
   int peel_mode;     /* 0 = subtract the recovered set's projections from the bins (only mode) */
-  int threads;       /* CTA size of the recovery kernel; 0 = library default */
+  int threads;       /* CTA size of the shared-memory-FFT recovery kernel (multiple of 32, <= 1024);
+                        0 = library default */
   int ctas_per_sm;   /* resident CTAs per SM for the persistent recovery grid; 0 = occupancy */
   int fp64_decisions;/* nonzero: evaluate T0..T2 in FP64 for every bin.  0 (default): evaluate in
                         FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a

@@ -43,8 +43,8 @@ def candidates(dims, params: Params):
     if warp_ok:
         for gm in (1, 2):
             out.append(replace(params, fft_path=2, gather_mode=gm, threads=0))
-    for th in (128, 256, 512):
-        if th > 4 * max(32, L_max):
+    for th in (128, 256, 512, 1024):
+        if th > 4 * max(32, L_max) or (th == 1024 and L_max < 512):
             continue
         for gm in (1, 3):
             out.append(replace(params, fft_path=1, gather_mode=gm, threads=th))

@@ -154,8 +154,8 @@ __device__ __forceinline__ void load_shape(Shape& sh, const Shape* __restrict__ 
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(512) k_recover(RecoverArgs A) {
+template <int D, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
@@ -1075,7 +1075,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
   if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
   if (pr.fft_path < 0 || pr.fft_path > 2) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 2]");
-  if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
+  if (pr.threads < 0 || pr.threads > 1024 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 1024]");
 
   auto* P = new (std::nothrow) fpssft_plan_s();
   if (!P) return fail(FPSSFT_ERR_ALLOC, "host allocation failed");
@@ -1222,8 +1222,10 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (pr.threads > 0) {
       P->threads = pr.threads;
     } else {
+      // one CTA per signal: up to 512 threads, 1024 when there are fewer signals than SMs
+      const int cap = batch < sms ? 1024 : 512;
       int t = 64;
-      while (t < P->L_max && t < 512) t <<= 1;
+      while (t < P->L_max && t < cap) t <<= 1;
       P->threads = t;
     }
   }
@@ -1254,7 +1256,8 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   // kernel attributes and the persistent grid
   fpssft_status st = dispatch_D(D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
-    const void* kfn = P->warp_path ? (const void*)k_recover_w<DD> : (const void*)k_recover<DD>;
+    const void* kfn = P->warp_path ? (const void*)k_recover_w<DD>
+                    : (P->threads > 512 ? (const void*)k_recover<DD, 1024> : (const void*)k_recover<DD, 512>);
     cudaError_t e2 = ensure_dynamic_smem(kfn, P->smem);
     if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
     int per_sm = 0;
@@ -1408,8 +1411,10 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
     constexpr int DD = decltype(Dc)::value;
     if (P->warp_path)
       k_recover_w<DD><<<P->grid, P->threads, P->smem, s>>>(A);
+    else if (P->threads > 512)
+      k_recover<DD, 1024><<<P->grid, P->threads, P->smem, s>>>(A);
     else
-      k_recover<DD><<<P->grid, P->threads, P->smem, s>>>(A);
+      k_recover<DD, 512><<<P->grid, P->threads, P->smem, s>>>(A);
     FPSSFT_CUDA_TRY(cudaGetLastError());
     return FPSSFT_OK;
   });
@@ -1904,13 +1909,13 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
   return dispatch_D(D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
     // raise (never lower) the kernel's dynamic shared-memory limit; shared with the plan path
-    FPSSFT_CUDA_TRY(ensure_dynamic_smem((const void*)k_recover<DD>, lay.total));
+    FPSSFT_CUDA_TRY(ensure_dynamic_smem((const void*)k_recover<DD, 512>, lay.total));
     int per_sm = 0;
-    FPSSFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover<DD>, threads, lay.total));
+    FPSSFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover<DD, 512>, threads, lay.total));
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (pr.ctas_per_sm > 0) per_sm = std::min(per_sm, pr.ctas_per_sm);
     const int grid = std::max(1, std::min(batch, per_sm * sms));
-    k_recover<DD><<<grid, threads, lay.total, s>>>(A);
+    k_recover<DD, 512><<<grid, threads, lay.total, s>>>(A);
     FPSSFT_CUDA_TRY(cudaGetLastError());
     return FPSSFT_OK;
   });

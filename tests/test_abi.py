@@ -49,7 +49,7 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"T": -1}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"theta0": -1.0}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"threads": 48}, _lib.ERR_INVALID),
-    (2, 1, [8, 8], {"threads": 1024}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"threads": 2048}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
     (2, 1, [8, 8], {"gather_mode": 4}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"fft_path": 3}, _lib.ERR_INVALID),

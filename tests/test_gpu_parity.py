@@ -402,3 +402,22 @@ def test_autotuned_launch_computes_the_same_sets():
     for b in range(wl.batch):
         n = int(ref.count[b])
         assert torch.equal(ref.k[b, :n], got.k[b, :n])
+
+
+def test_1024_thread_cta_equals_512_thread_cta_and_oracle():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("single_240x256")
+    outs = []
+    for th in (512, 1024):
+        p = configs.params_for(wl, fft_path=1, threads=th)
+        plan = Plan(wl.dims, p)
+        assert plan.info["threads"] == th
+        outs.append(plan.recover(*to_dev(wl)))
+        torch.cuda.synchronize()
+    a, b = outs
+    assert torch.equal(a.count, b.count) and torch.equal(a.iters, b.iters)
+    n = int(a.count[0])
+    assert torch.equal(a.k[0, :n], b.k[0, :n]) and torch.allclose(a.a[0, :n], b.a[0, :n], rtol=AMP_TOL, atol=0)
+    ref = O.recover(wl.cube(0), wl.alpha[0], wl.tau[0], oracle_params(configs.params_for(wl), 12))
+    k, aa = b.signal(0)
+    assert_same_set(k, aa, ref)
