@@ -421,3 +421,20 @@ def test_1024_thread_cta_equals_512_thread_cta_and_oracle():
     ref = O.recover(wl.cube(0), wl.alpha[0], wl.tau[0], oracle_params(configs.params_for(wl), 12))
     k, aa = b.signal(0)
     assert_same_set(k, aa, ref)
+
+
+@pytest.mark.parametrize("K,block", [(256, 0), (1280, 0), (1278, 3)])
+def test_fig2_trials_on_gpu_equal_the_oracle_trial_by_trial(K, block):
+    """The paper's Fig. 2 setting (256 x 256, T_max = 85): every trial's outcome and iteration count
+    on the GPU equals the oracle's."""
+    from paper_1711_11407_gb300 import fig2
+    trials = 12
+    r = fig2.run_point(K, block, trials=trials, seed=7)
+    for t in range(trials):
+        k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence([7, K, block, t]), (256, 256), K, fig2.T_MAX, block=block)
+        ref = O.recover(x.astype(np.complex64).astype(np.complex128), al, ta,
+                        O.Params(T=fig2.T_MAX, k_cap=2 * K + 64))
+        truth = np.sort(k[:, 0] * 256 + k[:, 1])
+        ok = ref.k.shape[0] == K and np.array_equal(ref.k[:, 0] * 256 + ref.k[:, 1], truth)
+        assert r["per_trial_success"][t] == ok, f"trial {t}"
+        assert r["iters"][t] == ref.iters, f"trial {t}: iterations {r['iters'][t]} vs oracle {ref.iters}"
