@@ -79,8 +79,9 @@ typedef struct {
                         guard band around a threshold -- the verdicts are the same either way */
   int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice (synchronous
                         through L1), 1 = synchronous through L1, 2 = synchronous cached in L2 only,
-                        3 = asynchronous copies of the next iteration's lines while the current
-                        one computes (needs a third line buffer in shared memory) */
+                        3 = asynchronous copies (cp.async) of the next iteration's lines into a
+                        shared-memory buffer while the current one computes.  On the register-FFT
+                        path modes 1 and 2 prefetch the next iteration into registers instead */
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
                         FFT (every L of the batch in {32, 64, 128, 256}) */
@@ -102,13 +103,17 @@ typedef struct {
   int twiddles_in_smem;
   int prefetch;       /* 1: the next iteration's lines are gathered while the current one computes */
   int fft_path;       /* 1: shared-memory FFT, one CTA per signal; 2: register FFT, one warp per line */
+  int global_workspace; /* 1: lines and recovered set too large for shared memory live in a
+                        per-CTA slice of plan-owned global workspace (fpssft_recover only) */
 } fpssft_plan_info;
 
 /* Create a plan for `batch` signals of dimension D with shapes dims (HOST int64 [batch][D],
  * each N_d >= 1).  Computes L_b = LCM(dims[b]) (Lemma 1), the mixed-radix FFT factorisation of
  * every distinct L, FP64-derived twiddle tables, the per-signal iteration budget and a
  * longest-first work order, and uploads them to device workspace owned by the plan.
- * Returns FPSSFT_ERR_UNSUPPORTED when a line of the batch does not fit one CTA's shared memory.
+ * When the D+1 lines or the recovered set do not fit one CTA's shared memory, fpssft_recover keeps
+ * them in plan-owned global workspace (2 x SM count slices); fpssft_project, fpssft_lines,
+ * fpssft_synth and fpssft_adjoint then return FPSSFT_ERR_UNSUPPORTED for that plan.
  * Must be called with the target device current. */
 fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch, const int64_t* dims,
                                  const fpssft_params* params);

@@ -69,7 +69,8 @@ def build(force=False, verbose=False):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("D", "batch", "L_max", "T_max", "k_cap", "hash_cap", "n_shapes",
-                                            "threads", "grid", "smem_bytes", "twiddles_in_smem", "prefetch", "fft_path")]
+                                            "threads", "grid", "smem_bytes", "twiddles_in_smem", "prefetch", "fft_path",
+                                            "global_workspace")]
 
 
 class CParams(ctypes.Structure):

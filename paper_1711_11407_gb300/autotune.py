@@ -3,7 +3,8 @@
 Candidates are the valid combinations of
   fft_path     1 (one CTA per signal, shared-memory mixed-radix FFT) or 2 (one warp per line,
                register FFT; only when every line length is 32, 64, 128 or 256),
-  gather_mode  1 (synchronous through L1), 2 (L2 only) or 3 (asynchronous prefetch; path 1 only),
+  gather_mode  1 (synchronous through L1), 2 (L2 only) or 3 (asynchronous prefetch: cp.async into
+               shared memory; on path 2 it replaces the register prefetch),
   threads      CTA size for path 1 (path 2 is fixed at 32 (D+1)).
 Each candidate is timed on the caller's own inputs with CUDA events (warm-up first, a buffer larger
 than L2 written between timed launches); the fastest wins.  Results are cached in a JSON file keyed
@@ -41,7 +42,7 @@ def candidates(dims, params: Params):
     L_max = max(Ls) if Ls else 1
     out = []
     if warp_ok:
-        for gm in (1, 2):
+        for gm in (1, 2, 3):
             out.append(replace(params, fft_path=2, gather_mode=gm, threads=0))
     for th in (128, 256, 512, 1024):
         if th > 4 * max(32, L_max) or (th == 1024 and L_max < 512):

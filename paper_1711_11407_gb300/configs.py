@@ -21,6 +21,7 @@ BUDGET = {
     "batched_64x64x64": dict(T=0, k_cap=1024),
     "uneven_2d": dict(T=0, k_cap=512),
     "images_1024x1024": dict(T=0, k_cap=4096),
+    "sparse_image_512x576": dict(T=0, k_cap=20000),
     "batched_64x64x64_ps": dict(T=0, k_cap=1024),
     "images_1024x1024_ps": dict(T=0, k_cap=4096),
 }

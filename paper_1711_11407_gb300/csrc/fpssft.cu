@@ -106,6 +106,8 @@ struct RecoverArgs {
   int prefetch;
   int gather_mode;
   int early_stop;
+  unsigned char* gm_ws;      // lines and recovered set in global memory (lines longer than shared memory)
+  size_t gm_stride;          // bytes of workspace per CTA
   Thresholds th;
   const int* init_count;
   int* out_k;
@@ -154,25 +156,29 @@ __device__ __forceinline__ void load_shape(Shape& sh, const Shape* __restrict__ 
   }
 }
 
-template <int D, int MAXT>
+// GM = true: the same kernel with the lines, the FFT partner and the recovered set in a per-CTA
+// slice of global workspace (L2-resident) instead of shared memory, for lines or sets too large
+// for one CTA's shared memory.  All device functions take generic pointers.
+template <int D, int MAXT, bool GM = false>
 __global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
 
+  unsigned char* base = GM ? A.gm_ws + (size_t)blockIdx.x * A.gm_stride : smem;
   const SmemLayout lay = recover_layout(D, A.L_max, A.k_cap, 1 << A.hash_bits, A.tw_smem != 0, A.prefetch != 0);
-  float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
-  float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
-  float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
+  float2* bufA = reinterpret_cast<float2*>(base + lay.bufA);
+  float2* bufB = reinterpret_cast<float2*>(base + lay.bufB);
+  float2* bufC = reinterpret_cast<float2*>(base + lay.bufC);
   const bool pf = A.prefetch != 0;
-  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  float2* tws = reinterpret_cast<float2*>(base + lay.tw);
   SetView set;
-  set.la = reinterpret_cast<float2*>(smem + lay.la);
-  set.lk = reinterpret_cast<int*>(smem + lay.lk);
-  set.lkey = reinterpret_cast<int*>(smem + lay.lkey);
-  set.hkey = reinterpret_cast<int*>(smem + lay.hkey);
-  set.hidx = reinterpret_cast<int*>(smem + lay.hidx);
+  set.la = reinterpret_cast<float2*>(base + lay.la);
+  set.lk = reinterpret_cast<int*>(base + lay.lk);
+  set.lkey = reinterpret_cast<int*>(base + lay.lkey);
+  set.hkey = reinterpret_cast<int*>(base + lay.hkey);
+  set.hidx = reinterpret_cast<int*>(base + lay.hidx);
   set.count = &s_count;
   set.k_cap = A.k_cap;
   set.hash_bits = A.hash_bits;
@@ -282,10 +288,10 @@ __global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
 // only the bins (bank-swizzled), the twiddles and the bucket set, so several times more signals
 // are resident per SM than with the shared-memory Stockham path.
 struct WLayout {
-  size_t bins, tw, head, la, lk, nxt, total;
+  size_t bins, tw, head, la, lk, nxt, stg, total;
 };
 
-static __host__ __device__ WLayout recover_layout_w(int D, int L_max, int k_cap) {
+static __host__ __device__ WLayout recover_layout_w(int D, int L_max, int k_cap, bool staged = false) {
   auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
   size_t P = 1;
   while (P < (size_t)k_cap) P <<= 1;
@@ -299,6 +305,7 @@ static __host__ __device__ WLayout recover_layout_w(int D, int L_max, int k_cap)
   w.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
   w.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
   w.nxt = off; off = al(off + (size_t)k_cap * sizeof(int));
+  w.stg = off; off = al(off + (staged ? lines : 0));
   w.total = off;
   return w;
 }
@@ -440,17 +447,21 @@ __device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh,
 // The iterations of one signal on the warp-FFT path.  Warp j owns line j.  The samples of
 // iteration t+1 are loaded into registers right after iteration t's FFT (the schedule is known in
 // advance), so their latency overlaps t's peel and decode.
-template <int D, int R>
+template <int D, int R, bool STAGED>
 __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
-                                         const float2* tws, const float2* __restrict__ x, const int* sched_a,
-                                         const int* sched_t, int T, int warp, int lane, float invL, int* s_ca,
-                                         int* s_ct, int* s_t0, int* s_ovf) {
+                                         const float2* tws, float2* stg, const float2* __restrict__ x,
+                                         const int* sched_a, const int* sched_t, int T, int warp, int lane,
+                                         float invL, int* s_ca, int* s_ct, int* s_t0, int* s_ovf) {
   const int L = sh.L;
-  float2 nxt[R];
+  float2 nxt[STAGED ? 1 : R];
+  float2* my_stg = stg + warp * L;
   if (T > 0) {
     int alr[D], tar[D];
     sched_row<D>(sh, sched_a, sched_t, alr, tar);
-    gather_line_regs<D, R>(nxt, x, sh, alr, tar, warp, lane);
+    if (STAGED)
+      gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
+    else
+      gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
   }
   int iters = 0;
   for (int t = 0; t < T; ++t) {
@@ -463,13 +474,22 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) set.head[m] = -1;
     float2 v[R];
+    if (STAGED) {
+      cp_async_wait<0>();
 #pragma unroll
-    for (int i = 0; i < R; ++i) v[i] = nxt[i];
-    fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);
+      for (int i = 0; i < R; ++i) v[i] = my_stg[lane + 32 * i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = nxt[STAGED ? 0 : i];
+    }
+    fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
     if (t + 1 < T) {
       int alr[D], tar[D];
       sched_row<D>(sh, al + D, ta + D, alr, tar);
-      gather_line_regs<D, R>(nxt, x, sh, alr, tar, warp, lane);
+      if (STAGED)
+        gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
+      else
+        gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
     }
     __syncthreads();
     if (threadIdx.x == 0) *s_t0 = 0;
@@ -481,6 +501,7 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
     const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
     if (stop) break;
   }
+  if (STAGED) cp_async_wait<0>();   // a copy issued past the last iteration lands before reuse
   return iters;
 }
 
@@ -488,15 +509,21 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
 #define FPSSFT_W_THREADS_PER_SM 640   // resident threads per SM the warp path's register budget targets
 #endif
 
-template <int D>
-__global__ void __launch_bounds__(32 * (D + 1), FPSSFT_W_THREADS_PER_SM / (32 * (D + 1))) k_recover_w(RecoverArgs A) {
+#ifndef FPSSFT_WS_THREADS_PER_SM
+#define FPSSFT_WS_THREADS_PER_SM 768   // same for the variant that stages the prefetch in shared memory
+#endif
+
+template <int D, bool STAGED>
+__global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_SM : FPSSFT_W_THREADS_PER_SM) / (32 * (D + 1)))
+    k_recover_w(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
-  const WLayout lay = recover_layout_w(D, A.L_max, A.k_cap);
+  const WLayout lay = recover_layout_w(D, A.L_max, A.k_cap, STAGED);
   float2* bins = reinterpret_cast<float2*>(smem + lay.bins);
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  float2* stg = reinterpret_cast<float2*>(smem + lay.stg);
   BucketSet set;
   set.lk = reinterpret_cast<int*>(smem + lay.lk);
   set.la = reinterpret_cast<float2*>(smem + lay.la);
@@ -551,10 +578,10 @@ __global__ void __launch_bounds__(32 * (D + 1), FPSSFT_W_THREADS_PER_SM / (32 * 
     const int* sched_t = A.tau + (size_t)b * A.sched_stride;
     int iters = 0;
     switch (R) {
-      case 1: iters = iterate_w<D, 1>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
-      case 2: iters = iterate_w<D, 2>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
-      case 4: iters = iterate_w<D, 4>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
-      default: iters = iterate_w<D, 8>(A, sh, set, bins, tws, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      case 1: iters = iterate_w<D, 1, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      case 2: iters = iterate_w<D, 2, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
     }
 
     const int count = min(s_count, A.k_cap);
@@ -947,6 +974,10 @@ struct fpssft_plan_s {
   bool tw_smem = true;
   bool prefetch = true;
   bool warp_path = false;   // k_recover_w (register FFT per line) instead of k_recover
+  bool gm_path = false;     // k_recover with lines and set in global workspace
+  bool lines_in_smem = true;   // fpssft_project / _lines / _adjoint / _synth usable
+  unsigned char* d_gm_ws = nullptr;
+  size_t gm_stride = 0;
   size_t smem = 0;
   size_t total_elems = 0;   // sum of N_b (for host staging)
   std::vector<Shape> shapes;
@@ -1038,6 +1069,7 @@ fpssft_status dispatch_D(int D, F&& f) {
 }
 
 void free_plan_memory(fpssft_plan_s* p) {
+  cudaFree(p->d_gm_ws);
   cudaFree(p->d_shapes);
   cudaFree(p->d_sig_shape);
   cudaFree(p->d_sig_T);
@@ -1181,18 +1213,18 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     const int R = sh.L / 32;
     warp_ok = warp_ok && sh.L % 32 == 0 && (R == 1 || R == 2 || R == 4 || R == 8);
   }
-  warp_ok = warp_ok && pr.k_cap < (1 << 20) && pr.gather_mode != 3;
+  warp_ok = warp_ok && pr.k_cap < (1 << 20);
   if (pr.fft_path == 2 && !warp_ok) {
     delete P;
     return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 2 needs every line length in {32, 64, 128, 256} and no prefetch");
   }
   if ((pr.fft_path == 2 || (pr.fft_path == 0 && warp_ok)) && batch > 0) {
-    const WLayout wl = recover_layout_w(D, P->L_max, pr.k_cap);
+    const WLayout wl = recover_layout_w(D, P->L_max, pr.k_cap, pr.gather_mode == 3);
     if (wl.total + sizeof(Shape) + 256 <= (size_t)optin) {
       P->warp_path = true;
       P->smem = wl.total;
       P->tw_smem = true;
-      P->prefetch = false;
+      P->prefetch = pr.gather_mode == 3;   // staged in shared memory by cp.async
       P->threads = 32 * (D + 1);
     } else if (pr.fft_path == 2) {
       delete P;
@@ -1203,22 +1235,28 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   // shared memory; drop them in that order if they do not fit
   const bool want_pf = pr.gather_mode == 3;
   SmemLayout lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, want_pf);
-  P->tw_smem = true;
-  P->prefetch = want_pf;
+  if (!P->warp_path) {
+    P->tw_smem = true;
+    P->prefetch = want_pf;
+  }
   if (lay.total + static_reserve > (size_t)optin) {
     lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, false);
-    P->prefetch = false;
+    if (!P->warp_path) P->prefetch = false;
   }
   if (lay.total + static_reserve > (size_t)optin) {
     lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false, false);
-    P->tw_smem = false;
+    if (!P->warp_path) P->tw_smem = false;
   }
   if (!P->warp_path && lay.total + static_reserve > (size_t)optin) {
-    delete P;
-    return fail(FPSSFT_ERR_UNSUPPORTED, "lines + recovered set exceed one CTA's shared memory (L_max or k_cap too large)");
+    // lines or set too large for shared memory: keep them in a per-CTA slice of global workspace
+    P->gm_path = true;
+    P->tw_smem = false;
+    P->prefetch = false;
+    lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false, false);
+    P->gm_stride = (lay.total + 255) & ~size_t(255);
   }
   if (!P->warp_path) {
-    P->smem = lay.total;
+    P->smem = P->gm_path ? 0 : lay.total;
     if (pr.threads > 0) {
       P->threads = pr.threads;
     } else {
@@ -1256,7 +1294,9 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   // kernel attributes and the persistent grid
   fpssft_status st = dispatch_D(D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
-    const void* kfn = P->warp_path ? (const void*)k_recover_w<DD>
+    if (P->gm_path) P->threads = std::min(P->threads, 512);
+    const void* kfn = P->warp_path ? (P->prefetch ? (const void*)k_recover_w<DD, true> : (const void*)k_recover_w<DD, false>)
+                    : P->gm_path ? (const void*)k_recover<DD, 512, true>
                     : (P->threads > 512 ? (const void*)k_recover<DD, 1024> : (const void*)k_recover<DD, 512>);
     cudaError_t e2 = ensure_dynamic_smem(kfn, P->smem);
     if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
@@ -1266,11 +1306,19 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
     P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
+    if (P->gm_path) {   // cap the persistent grid: every CTA owns a workspace slice
+      P->grid = std::max(1, std::min(batch, 2 * P->sm_count));
+      const size_t bytes = (size_t)P->grid * P->gm_stride;
+      const cudaError_t ea = cudaMalloc(&P->d_gm_ws, bytes);
+      if (ea != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, std::string("workspace for long lines: ") + cudaGetErrorString(ea));
+    }
     const size_t ls = line_smem(DD, P->L_max);
-    if (ls > (size_t)optin) return fail(FPSSFT_ERR_UNSUPPORTED, "lines exceed shared memory");
-    e2 = ensure_dynamic_smem((const void*)k_project<DD>, ls);
-    if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_adjoint_project<DD>, ls);
-    if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_synth<DD>, ls / 2);
+    P->lines_in_smem = ls + sizeof(Shape) + 256 <= (size_t)optin;
+    if (P->lines_in_smem) {
+      e2 = ensure_dynamic_smem((const void*)k_project<DD>, ls);
+      if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_adjoint_project<DD>, ls);
+      if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_synth<DD>, ls / 2);
+    }
     const size_t ds = (size_t)P->p.k_cap * (sizeof(float2) + (DD + 1) * sizeof(int)) + (size_t)2 * (1 << P->hash_bits) * sizeof(int);
     if (e2 == cudaSuccess && ds <= (size_t)optin) e2 = ensure_dynamic_smem((const void*)k_decode<DD>, ds);
     if (e2 == cudaSuccess && ds <= (size_t)optin) e2 = ensure_dynamic_smem((const void*)k_finalize<DD>, ds);
@@ -1313,6 +1361,7 @@ extern "C" fpssft_status fpssft_plan_get_info(fpssft_plan_t P, fpssft_plan_info*
   info->twiddles_in_smem = P->tw_smem ? 1 : 0;
   info->prefetch = P->prefetch ? 1 : 0;
   info->fft_path = P->warp_path ? 2 : 1;
+  info->global_workspace = P->gm_path ? 1 : 0;
   return FPSSFT_OK;
 }
 
@@ -1341,6 +1390,7 @@ static fpssft_status launch_project(fpssft_plan_t P, const void* cubes, const in
   if (n_sched < 0) return fail(FPSSFT_ERR_INVALID, "n_sched must be >= 0");
   if (P->batch == 0 || n_sched == 0) return FPSSFT_OK;
   if (!cubes || !offsets || !alpha || !tau || !out) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  if (!P->lines_in_smem) return fail(FPSSFT_ERR_UNSUPPORTED, "lines of this plan exceed one CTA's shared memory");
   ProjectArgs A;
   A.cubes = static_cast<const float2*>(cubes);
   A.offsets = offsets;
@@ -1399,6 +1449,8 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   A.prefetch = P->prefetch ? 1 : 0;
   A.gather_mode = P->p.gather_mode;
   A.early_stop = P->p.early_stop;
+  A.gm_ws = P->d_gm_ws;
+  A.gm_stride = P->gm_stride;
   A.th = P->thresholds();
   A.init_count = init_count;
   A.out_k = out_k;
@@ -1409,12 +1461,18 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   FPSSFT_CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
   return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
-    if (P->warp_path)
-      k_recover_w<DD><<<P->grid, P->threads, P->smem, s>>>(A);
-    else if (P->threads > 512)
+    if (P->warp_path) {
+      if (P->prefetch)
+        k_recover_w<DD, true><<<P->grid, P->threads, P->smem, s>>>(A);
+      else
+        k_recover_w<DD, false><<<P->grid, P->threads, P->smem, s>>>(A);
+    } else if (P->gm_path) {
+      k_recover<DD, 512, true><<<P->grid, P->threads, 0, s>>>(A);
+    } else if (P->threads > 512) {
       k_recover<DD, 1024><<<P->grid, P->threads, P->smem, s>>>(A);
-    else
+    } else {
       k_recover<DD, 512><<<P->grid, P->threads, P->smem, s>>>(A);
+    }
     FPSSFT_CUDA_TRY(cudaGetLastError());
     return FPSSFT_OK;
   });
@@ -1491,6 +1549,7 @@ extern "C" fpssft_status fpssft_synth(fpssft_plan_t P, const int32_t* alpha, con
   if (n_sched < 0 || accumulate < -1 || accumulate > 1) return fail(FPSSFT_ERR_INVALID, "bad n_sched or accumulate");
   if (P->batch == 0 || n_sched == 0) return FPSSFT_OK;
   if (!alpha || !tau || !k || !a || !count || !bins) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  if (!P->lines_in_smem) return fail(FPSSFT_ERR_UNSUPPORTED, "lines of this plan exceed one CTA's shared memory");
   SynthArgs A;
   A.alpha = alpha;
   A.tau = tau;
@@ -1577,6 +1636,7 @@ extern "C" fpssft_status fpssft_adjoint(fpssft_plan_t P, fpssft_adj_mode mode, c
   if (mode == FPSSFT_ADJ_PROJECT) {
     if (n_sched == 0) return FPSSFT_OK;
     if (!grad_bins || !offsets || !alpha || !tau || !grad_out) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+    if (!P->lines_in_smem) return fail(FPSSFT_ERR_UNSUPPORTED, "lines of this plan exceed one CTA's shared memory");
     AdjProjectArgs A;
     A.g = static_cast<const float2*>(grad_bins);
     A.offsets = offsets;

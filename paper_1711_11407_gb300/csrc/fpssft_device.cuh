@@ -719,6 +719,33 @@ __device__ __forceinline__ void gather_line_regs(float2 (&v)[R], const float2* _
   }
 }
 
+// Asynchronous copy of line j's samples into shared memory: lane l copies samples l + 32 i into
+// stg[l + 32 i].  After cp.async.wait_group the lane reads back exactly what it copied itself, so
+// no barrier is needed.
+template <int D, int R>
+__device__ __forceinline__ void gather_line_async(float2* stg, const float2* __restrict__ x, const Shape& sh,
+                                                  const int* al, const int* ta, int j, int lane) {
+  int n[D], stepn[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    n[d] = fmod_(al[d] * lane + ta[d] + (j == d + 1 ? 1 : 0), sh.fdims[d]);
+    stepn[d] = fmod_(al[d] * 32, sh.fdims[d]);
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int base = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) base += n[d] * sh.strides[d];
+    cp_async8(stg + lane + 32 * i, x + base);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      n[d] += stepn[d];
+      if (n[d] >= sh.dims[d]) n[d] -= sh.dims[d];
+    }
+  }
+  cp_async_commit();
+}
+
 // The recovered set of the warp-FFT kernel: dense list (lk, la) and per-iteration buckets built by
 // the peel (head[m] -> first entry whose bin is m, nxt[i] -> next entry of the same bin).  A
 // frequency decoded from bin m that is already in the set must lie in bucket m (its bin is m by

@@ -11,8 +11,10 @@ complex amplitudes a_k != 0.  The cube is stored C-order (last dimension fastest
 Line schedule (Sec. 2.2 and Sec. 2.3): every iteration draws a slope alpha and an offset tau in
 X_D = [N_0] x ... x [N_{D-1}].  Slopes are drawn uniformly and rejected until the projection
 k -> [sum_d (L/N_d) alpha_d k_d]_L is onto Z_L (every bin receives N/L frequencies, the property
-Lemma 2 proves for its set A in 2-D); the optional policy "lemma2" draws from A itself.  The
-schedule is an input of the method: both implementations receive the same integers.
+Lemma 2 proves for its set A in 2-D); the optional policy "lemma2" draws from A itself, and
+"axis" uses the unit slopes e_0, e_1, ... in turn (the rows and columns of the row/column SFT the
+paper compares against, Sec. 2.1).  The schedule is an input of the method: both implementations
+receive the same integers.
 """
 from __future__ import annotations
 
@@ -66,12 +68,15 @@ def draw_schedule(rng, dims, T, policy="uniform"):
     alpha = np.zeros((T, D), np.int32)
     tau = np.zeros((T, D), np.int32)
     for t in range(T):
-        for _ in range(100000):
-            a = [int(rng.integers(0, n)) for n in dims]
-            if _admissible(a, dims, policy):
-                break
-        else:  # pragma: no cover - only reachable for degenerate policies
-            raise RuntimeError(f"no admissible slope found for dims {dims}")
+        if policy == "axis":        # rows and columns in turn: the axis lines of the row/column SFT
+            a = [1 if d == t % D else 0 for d in range(D)]
+        else:
+            for _ in range(100000):
+                a = [int(rng.integers(0, n)) for n in dims]
+                if _admissible(a, dims, policy):
+                    break
+            else:  # pragma: no cover - only reachable for degenerate policies
+                raise RuntimeError(f"no admissible slope found for dims {dims}")
         alpha[t] = a
         tau[t] = [int(rng.integers(0, n)) for n in dims]
     return alpha, tau
@@ -128,7 +133,7 @@ def draw_frequencies(rng, dims, K, clusters=0, sigma=0.0, block=0):
 
 def draw_amplitudes(rng, K, mode="unit"):
     """Complex amplitudes with uniform phase.  mode: 'unit' (|a| = 1), 'uniform' (|a| ~ U[0.5, 1.5]),
-    'lognormal' (|a| = exp(N(0, 0.5^2)))."""
+    'lognormal' (|a| = exp(N(0, 0.5^2))), 'uniform_real' (real, U[0.5, 1.5])."""
     phase = rng.uniform(0.0, 2.0 * np.pi, size=K)
     if mode == "unit":
         mag = np.ones(K)
@@ -136,6 +141,8 @@ def draw_amplitudes(rng, K, mode="unit"):
         mag = rng.uniform(0.5, 1.5, size=K)
     elif mode == "lognormal":
         mag = np.exp(rng.normal(0.0, 0.5, size=K))
+    elif mode == "uniform_real":     # positive real intensities U[0.5, 1.5] (pixels of an image)
+        return rng.uniform(0.5, 1.5, size=K) + 0j
     else:
         raise ValueError(f"unknown amplitude mode {mode!r}")
     return mag * np.exp(1j * phase)
@@ -236,6 +243,10 @@ WORKLOADS = {
                       K=lambda N: -(-N // 200), T=_budget, amp="unit"),
     "images_1024x1024": dict(shapes=[(1024, 1024)], batch=64, K=lambda N: 2000, T=_budget, amp="lognormal",
                              clusters=20, sigma_bins=10.0, snr_db=5.0),
+    # a sparse image of the size of the paper's Fig. 3 (512 x 576, L = LCM = 4608): blobs of
+    # non-zero "pixels" (frequencies) with positive intensities
+    "sparse_image_512x576": dict(shapes=[(512, 576)], batch=8, K=lambda N: 8411, T=_budget, amp="uniform_real",
+                                 clusters=60, sigma_bins=12.0),
     # the noisy workloads with the SNR read per sinusoid (sigma^2 = mean |a|^2 / 10^(snr/10))
     "batched_64x64x64_ps": dict(shapes=[(64, 64, 64)], batch=256, K=lambda N: 500, T=_budget, amp="unit",
                                 snr_db=10.0, snr_mode="per_sinusoid"),
@@ -243,7 +254,8 @@ WORKLOADS = {
                                 clusters=20, sigma_bins=10.0, snr_db=5.0, snr_mode="per_sinusoid"),
 }
 WORKLOAD_IDS = {1: "single_128x128", 2: "single_240x256", 3: "batched_64x64x64", 4: "uneven_2d",
-                5: "images_1024x1024", 13: "batched_64x64x64_ps", 15: "images_1024x1024_ps"}
+                5: "images_1024x1024", 6: "sparse_image_512x576", 13: "batched_64x64x64_ps",
+                15: "images_1024x1024_ps"}
 
 
 def make_workload(name, seed=None, batch=None, *, shapes=None, K=None, T=None, snr_db="default",

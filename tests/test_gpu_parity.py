@@ -366,20 +366,21 @@ def test_register_fft_path_equals_shared_memory_path(case):
         wl = small_batch(shapes, 8, K=lambda N: max(2, min(40, N // 64)), T=12)
         T = 12
     outs = []
-    for path in (1, 2):
-        p = configs.params_for(wl, fft_path=path, k_cap=512)
+    for path, gm in ((1, 1), (2, 1), (2, 3)):
+        p = configs.params_for(wl, fft_path=path, gather_mode=gm, k_cap=512)
         if T is not None:
             p.T = T
         plan = Plan(wl.dims, p)
-        assert plan.info["fft_path"] == path
+        assert plan.info["fft_path"] == path and plan.info["prefetch"] == (gm == 3)
         outs.append(plan.recover(*to_dev(wl)))
         torch.cuda.synchronize()
-    a, b = outs
-    assert torch.equal(a.count, b.count) and torch.equal(a.iters, b.iters) and torch.equal(a.status, b.status)
-    for i in range(wl.batch):
-        n = int(a.count[i])
-        assert torch.equal(a.k[i, :n], b.k[i, :n])
-        assert torch.allclose(a.a[i, :n], b.a[i, :n], rtol=AMP_TOL, atol=0)
+    a = outs[0]
+    for b in outs[1:]:
+        assert torch.equal(a.count, b.count) and torch.equal(a.iters, b.iters) and torch.equal(a.status, b.status)
+        for i in range(wl.batch):
+            n = int(a.count[i])
+            assert torch.equal(a.k[i, :n], b.k[i, :n])
+            assert torch.allclose(a.a[i, :n], b.a[i, :n], rtol=AMP_TOL, atol=0)
     for i in range(min(4, wl.batch)):
         Ti = int(wl.T[i]) if T is None else T
         ref = O.recover(wl.cube(i), wl.alpha[i, :Ti], wl.tau[i, :Ti], oracle_params(p, Ti))
@@ -438,3 +439,54 @@ def test_fig2_trials_on_gpu_equal_the_oracle_trial_by_trial(K, block):
         ok = ref.k.shape[0] == K and np.array_equal(ref.k[:, 0] * 256 + ref.k[:, 1], truth)
         assert r["per_trial_success"][t] == ok, f"trial {t}"
         assert r["iters"][t] == ref.iters, f"trial {t}: iterations {r['iters'][t]} vs oracle {ref.iters}"
+
+
+def test_long_lines_and_large_sets_use_global_workspace_and_match_oracle():
+    """512 x 576 (L = 4608, the size of the paper's Fig. 3 image, K = 8411) and a 240 x 256 signal
+    with a 20000-entry set: both exceed one CTA's shared memory, so the plan keeps lines and set in
+    global workspace; the recovered sets equal the oracle's."""
+    from paper_1711_11407_gb300.api import Plan
+    for wl, kcap in ((S.make_workload("sparse_image_512x576", batch=2), 20000),
+                     (S.make_workload("single_240x256"), 20000)):
+        p = configs.params_for(wl, k_cap=kcap)
+        plan = Plan(wl.dims, p)
+        assert plan.info["global_workspace"] == 1
+        out = plan.recover(*to_dev(wl))
+        torch.cuda.synchronize()
+        for b in range(wl.batch):
+            T = int(plan.T[b])
+            ref = O.recover(wl.cube(b), wl.alpha[b, :T], wl.tau[b, :T], oracle_params(p, T))
+            k, a = out.signal(b)
+            assert_same_set(k, a, ref, f"{wl.name} signal {b}")
+            assert int(out.iters[b]) == ref.iters
+
+
+def test_axis_schedule_stays_in_deadlock_where_random_slopes_recover():
+    """Rows and columns only (the row/column SFT's lines, Sec. 2.1) against random slopes on the
+    Fig. 1 deadlock instance and at K = 2 N0 on 256 x 256: the GPU matches the oracle either way."""
+    import pins
+    from paper_1711_11407_gb300.api import Plan
+    dims, k, a, _ = pins.load_deadlock()
+    x = S.synthesize_cube(dims, k, a).astype(np.complex64)
+    d = dev()
+    for policy, expect in (("axis", 0), ("uniform", 4)):
+        al, ta = S.draw_schedule(np.random.default_rng(3), dims, 6, policy)
+        plan = Plan(np.array([dims], np.int64), configs.params_for(S.make_workload("single_128x128"), T=6, k_cap=16))
+        out = plan.recover(torch.from_numpy(x.reshape(-1)).to(d), torch.zeros(1, dtype=torch.int64, device=d),
+                           torch.from_numpy(al[None]).to(d), torch.from_numpy(ta[None]).to(d))
+        torch.cuda.synchronize()
+        ref = O.recover(x.astype(np.complex128), al, ta, O.Params(T=6, k_cap=16))
+        assert int(out.count[0]) == ref.k.shape[0] == expect, policy
+    ok = {}
+    for policy in ("axis", "uniform"):
+        wl = S.make_workload("uneven_2d", batch=6, shapes=[(256, 256)], K=lambda N: 512, T=85, policy=policy)
+        p = configs.params_for(wl, T=85, k_cap=1100)
+        out = Plan(wl.dims, p).recover(*to_dev(wl))
+        torch.cuda.synchronize()
+        ok[policy] = 0
+        for b in range(wl.batch):
+            ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, 85))
+            kk, aa = out.signal(b)
+            assert_same_set(kk, aa, ref, f"{policy} {b}")
+            ok[policy] += int(kk.shape[0] == 512)
+    assert ok["axis"] == 0 and ok["uniform"] == 6
