@@ -498,9 +498,11 @@ __device__ __forceinline__ int classify_fp32(const float2 s0, const float2* sd, 
   return kAccept;
 }
 
+// Out of line: it runs only for the rare bins inside a guard band, and keeping its FP64 values
+// out of the callers' register allocation lets more CTAs stay resident.
 template <int D>
-__device__ __forceinline__ int classify_fp64(const float2 s0, const float2* sd, const Shape& sh,
-                                             const Thresholds& th, int* k, bool* t0_counted) {
+__device__ __noinline__ int classify_fp64(const float2 s0, const float2* sd, const Shape& sh,
+                                          const Thresholds& th, int* k, bool* t0_counted) {
   const double kTwoPi = 6.283185307179586476925286766559;
   const double e0 = (double)s0.x * s0.x + (double)s0.y * s0.y;
   if (!(e0 > th.th0sq)) return kReject;                               // T0
