@@ -365,9 +365,9 @@ __device__ __forceinline__ void peel_set_w(float2* bins, const Shape& sh, const 
 template <int D>
 __device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& sh, const BucketSet& s, const int* ca,
                                               const int* ct, const float2* __restrict__ tw, const Thresholds& th,
-                                              int* t0, int* ovf) {
+                                              int* t0, int* ovf, int* accepted) {
   const int L = sh.L;
-  int my_t0 = 0;
+  int my_t0 = 0, my_acc = 0;
   bool my_ovf = false;
   for (int m = threadIdx.x; m < L; m += blockDim.x) {
     const int pm = swz(m);
@@ -393,9 +393,11 @@ __device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& s
     }
     if (fmod_(msum, sh.fL) != m) continue;                            // T3
     const float2 a = cmul(s0, tw[fmod_(psum, sh.fL)]);                // a = s_0 W^-p
+    ++my_acc;
     if (!bucket_insert<D>(s, m, k, a)) my_ovf = true;
   }
   if (my_t0) atomicAdd(t0, my_t0);
+  if (my_acc) atomicAdd(accepted, my_acc);
   if (my_ovf) atomicOr(ovf, 1);
 }
 
@@ -447,14 +449,20 @@ __device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh,
 // The iterations of one signal on the warp-FFT path.  Warp j owns line j.  The samples of
 // iteration t+1 are loaded into registers right after iteration t's FFT (the schedule is known in
 // advance), so their latency overlaps t's peel and decode.
+// When every bin that passed T0 in iteration t-1 was decoded and merged, the set is most likely
+// complete and iteration t will find nothing (the early stop): iteration t then does not prefetch
+// t+1.  If the guess is wrong, iteration t+1 gathers its samples synchronously; the results do not
+// depend on the guess.
 template <int D, int R, bool STAGED>
 __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
                                          const float2* tws, float2* stg, const float2* __restrict__ x,
                                          const int* sched_a, const int* sched_t, int T, int warp, int lane,
-                                         float invL, int* s_ca, int* s_ct, int* s_t0, int* s_ovf) {
+                                         float invL, int* s_ca, int* s_ct, int* s_t0, int* s_ovf, int* s_acc) {
   const int L = sh.L;
   float2 nxt[STAGED ? 1 : R];
   float2* my_stg = stg + warp * L;
+  bool have_next = false;      // samples of the current iteration already requested
+  bool likely_done = false;    // every T0 bin of the previous iteration was accepted
   if (T > 0) {
     int alr[D], tar[D];
     sched_row<D>(sh, sched_a, sched_t, alr, tar);
@@ -462,6 +470,7 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
       gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
     else
       gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
+    have_next = true;
   }
   int iters = 0;
   for (int t = 0; t < T; ++t) {
@@ -474,7 +483,11 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) set.head[m] = -1;
     float2 v[R];
-    if (STAGED) {
+    if (!have_next) {
+      int alr[D], tar[D];
+      sched_row<D>(sh, al, ta, alr, tar);
+      gather_line_regs<D, R>(v, x, sh, alr, tar, warp, lane);
+    } else if (STAGED) {
       cp_async_wait<0>();
 #pragma unroll
       for (int i = 0; i < R; ++i) v[i] = my_stg[lane + 32 * i];
@@ -483,7 +496,8 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
       for (int i = 0; i < R; ++i) v[i] = nxt[STAGED ? 0 : i];
     }
     fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
-    if (t + 1 < T) {
+    have_next = t + 1 < T && !likely_done;
+    if (have_next) {
       int alr[D], tar[D];
       sched_row<D>(sh, al + D, ta + D, alr, tar);
       if (STAGED)
@@ -492,14 +506,18 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
         gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
     }
     __syncthreads();
-    if (threadIdx.x == 0) *s_t0 = 0;
+    if (threadIdx.x == 0) {
+      *s_t0 = 0;
+      *s_acc = 0;
+    }
     peel_set_w<D>(bins, sh, set, min(*set.count, A.k_cap), s_ca, s_ct, tws);
     __syncthreads();
-    decode_bins_w<D>(bins, sh, set, s_ca, s_ct, tws, A.th, s_t0, s_ovf);
+    decode_bins_w<D>(bins, sh, set, s_ca, s_ct, tws, A.th, s_t0, s_ovf, s_acc);
     __syncthreads();
     iters = t + 1;
     const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
     if (stop) break;
+    likely_done = A.early_stop && *s_acc == *s_t0;
   }
   if (STAGED) cp_async_wait<0>();   // a copy issued past the last iteration lands before reuse
   return iters;
@@ -518,7 +536,7 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
     k_recover_w(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
-  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
+  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n, s_acc;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
   const WLayout lay = recover_layout_w(D, A.L_max, A.k_cap, STAGED);
   float2* bins = reinterpret_cast<float2*>(smem + lay.bins);
@@ -578,10 +596,10 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
     const int* sched_t = A.tau + (size_t)b * A.sched_stride;
     int iters = 0;
     switch (R) {
-      case 1: iters = iterate_w<D, 1, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
-      case 2: iters = iterate_w<D, 2, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
-      case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
-      default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf); break;
+      case 1: iters = iterate_w<D, 1, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 2: iters = iterate_w<D, 2, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
     }
 
     const int count = min(s_count, A.k_cap);
