@@ -154,7 +154,10 @@ fpssft_status fpssft_lines(fpssft_plan_t plan, const void* cubes, const int64_t*
  *                row-major linear frequency index.
  *   out_iters:   iterations whose lines were sampled.
  *   out_status:  FPSSFT_OK or FPSSFT_ERR_CAPACITY per signal.
- * Allocates nothing; the caller's buffers and the plan's workspace are the only memory used. */
+ * Allocates nothing; the caller's buffers and the plan's workspace are the only memory used.
+ * `cubes` may also point to pinned (page-locked, mapped) host memory: the gather then reads the
+ * samples it needs over the host link (on GB300 the cache-coherent NVLink-C2C) instead of the
+ * caller copying every cube to the device first. */
 fpssft_status fpssft_recover(fpssft_plan_t plan, const void* cubes, const int64_t* offsets,
                              const int32_t* alpha, const int32_t* tau, const int32_t* init_count,
                              int32_t* out_k, void* out_a, int32_t* out_count, int32_t* out_iters,

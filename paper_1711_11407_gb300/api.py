@@ -159,6 +159,23 @@ class Plan:
                                            _ptr(out.iters), _ptr(out.status), _stream(stream)))
         return out
 
+    def recover_mapped(self, host_cubes, offsets, alpha, tau, out: RecoverOutput | None = None, init_count=None,
+                       stream=None):
+        """fpssft_recover with the cubes left in pinned host memory: the gather reads the samples it
+        needs over the host link (no copy of the cubes); offsets, schedule and outputs are on the
+        device.  host_cubes must be a contiguous pinned CPU complex64 tensor."""
+        if not isinstance(host_cubes, torch.Tensor) or host_cubes.is_cuda or host_cubes.dtype != torch.complex64 \
+                or not host_cubes.is_contiguous() or not host_cubes.is_pinned():
+            raise ValueError("host_cubes must be a contiguous pinned CPU complex64 tensor")
+        _need(offsets, torch.int64, "offsets")
+        self._sched(alpha, tau, rows=self.T_max)
+        if out is None:
+            out = self.alloc_output(offsets.device)
+        _lib.check(self.lib.fpssft_recover(self.handle, _ptr(host_cubes), _ptr(offsets), _ptr(alpha), _ptr(tau),
+                                           _ptr(init_count), _ptr(out.k), _ptr(out.a), _ptr(out.count),
+                                           _ptr(out.iters), _ptr(out.status), _stream(stream)))
+        return out
+
     def recover_host(self, cubes, offsets, alpha, tau, out=None, init_count=None, stream=None):
         """fpssft_recover_host on host arrays (numpy or pinned CPU tensors); returns host outputs."""
         def host(t, dtype):

@@ -490,3 +490,21 @@ def test_axis_schedule_stays_in_deadlock_where_random_slopes_recover():
             assert_same_set(kk, aa, ref, f"{policy} {b}")
             ok[policy] += int(kk.shape[0] == 512)
     assert ok["axis"] == 0 and ok["uniform"] == 6
+
+
+def test_recovery_reading_cubes_in_place_from_pinned_host_memory():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=96)
+    plan = Plan(wl.dims, configs.params_for(wl))
+    cubes, offs, al, ta = to_dev(wl)
+    ref = plan.recover(cubes, offs, al, ta)
+    host = torch.from_numpy(wl.cubes).pin_memory()
+    got = plan.recover_mapped(host, offs, al, ta)
+    torch.cuda.synchronize()
+    assert torch.equal(ref.count, got.count) and torch.equal(ref.iters, got.iters)
+    for b in range(wl.batch):
+        n = int(ref.count[b])
+        assert torch.equal(ref.k[b, :n], got.k[b, :n])
+        assert torch.allclose(ref.a[b, :n], got.a[b, :n], rtol=AMP_TOL, atol=0)
+    with pytest.raises(ValueError):
+        plan.recover_mapped(torch.from_numpy(wl.cubes), offs, al, ta)      # not pinned
