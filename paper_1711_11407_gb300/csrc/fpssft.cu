@@ -3,9 +3,11 @@
 // Paper: Wang, Patel, Petropulu, "FPS-SFT: A Multi-dimensional Sparse Fourier Transform Based on
 // the Fourier Projection-slice Theorem", arXiv 1711.11407.  The iteration of Sec. 2.2 (sample the
 // D+1 lines, L-point DFT, subtract the recovered set, decode 1-sparse bins, merge) runs inside one
-// persistent kernel: each CTA pulls a signal from a longest-first queue and keeps its lines, bins,
-// twiddles and recovered set in shared memory for all of that signal's iterations, so the only
-// global traffic per iteration is the (D+1) L sample gather.
+// persistent launch for a whole batch: every signal is owned by one CTA for all its iterations,
+// with its bins, twiddles and recovered set on chip, so the only global traffic per iteration is
+// the (D+1) L sample gather.  Two kernels: k_recover_w (one warp per line, register FFT, for
+// L in {32, 64, 128, 256}) and k_recover (shared-memory mixed-radix FFT, any L; with a global-
+// workspace variant for lines or sets too large for shared memory).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -417,38 +419,9 @@ __device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh,
     }
   }
   __syncthreads();
-  const int n = *n_out;
-  int P = 1;
-  while (P < n) P <<= 1;
-  for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
-    skey[i] = 0x7fffffff;
-    sidx[i] = -1;
-  }
-  __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const bool up = (i & k) == 0;
-          const int ki = skey[i], kj = skey[ixj];
-          if ((ki > kj) == up) {
-            skey[i] = kj;
-            skey[ixj] = ki;
-            const int t = sidx[i];
-            sidx[i] = sidx[ixj];
-            sidx[ixj] = t;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
+  bitonic_sort_pairs(skey, sidx, *n_out);
 }
 
-// The iterations of one signal on the warp-FFT path.  Warp j owns line j.  The samples of
-// iteration t+1 are loaded into registers right after iteration t's FFT (the schedule is known in
-// advance), so their latency overlaps t's peel and decode.
 // When every bin that passed T0 in iteration t-1 was decoded and merged, the set is most likely
 // complete and iteration t will find nothing (the early stop): iteration t then does not prefetch
 // t+1.  If the guess is wrong, iteration t+1 gathers its samples synchronously; the results do not
@@ -776,7 +749,6 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
       s_ovf = 0;
     }
     __syncthreads();
-    const int L = sh.L;
     if (threadIdx.x < D) {
       const int d = threadIdx.x;
       s_ca[d] = cmodL(sh, d, A.alpha[b * D + d]);

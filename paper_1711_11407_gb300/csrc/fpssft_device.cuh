@@ -582,23 +582,11 @@ __device__ __forceinline__ bool keep_amplitude(float2 a, const Thresholds& th) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Output: drop |a| <= theta0 and sort by linear index (bitonic sort in shared memory)
+// Output: drop |a| <= theta0 and sort by linear index (bitonic sort)
 // ------------------------------------------------------------------------------------------------
-// skey/sidx need pow2ceil(count) entries.  Returns the number of kept entries (in *n_out) with
-// sidx[r] the list position of the r-th smallest key.
-__device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thresholds& th, int* skey,
-                                          int* sidx, int* n_out) {
-  if (threadIdx.x == 0) *n_out = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    if (keep_amplitude(s.la[i], th)) {
-      const int pos = atomicAdd(n_out, 1);
-      skey[pos] = s.lkey[i];
-      sidx[pos] = i;
-    }
-  }
-  __syncthreads();
-  const int n = *n_out;
+// Sort (skey, sidx) pairs by key, n of them, CTA-cooperatively; the arrays need pow2ceil(n)
+// entries (padding gets the largest key).  Keys are unique, so the order is deterministic.
+__device__ __forceinline__ void bitonic_sort_pairs(int* skey, int* sidx, int n) {
   int P = 1;
   while (P < n) P <<= 1;
   for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
@@ -625,6 +613,23 @@ __device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thr
       __syncthreads();
     }
   }
+}
+
+// Compact the entries with |a| > theta0 into (skey, sidx) and sort them by linear index: on return
+// *n_out is the number kept and sidx[r] the list position of the r-th smallest key.
+__device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thresholds& th, int* skey, int* sidx,
+                                          int* n_out) {
+  if (threadIdx.x == 0) *n_out = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    if (keep_amplitude(s.la[i], th)) {
+      const int pos = atomicAdd(n_out, 1);
+      skey[pos] = s.lkey[i];
+      sidx[pos] = i;
+    }
+  }
+  __syncthreads();
+  bitonic_sort_pairs(skey, sidx, *n_out);
 }
 
 }  // namespace fpssft
