@@ -97,6 +97,8 @@ class Plan:
                                                     Ts.ctypes.data_as(ctypes.c_void_p)))
         self.L = Ls[: self.batch]
         self.T = Ts[: self.batch]
+        self.N = np.prod(dims, axis=1).astype(np.int64) if self.batch else np.zeros(0, np.int64)
+        self._validated = set()
 
     def close(self):
         if getattr(self, "handle", None):
@@ -119,6 +121,25 @@ class Plan:
             raise ValueError(f"schedule must have {rows} rows per signal")
         return alpha.shape[1]
 
+    def _check_extent(self, cubes, offsets):
+        """Every cube must lie inside `cubes`: offsets[b] >= 0 and offsets[b] + N_b <= cubes.numel().
+        The kernels trust the offsets, so they are checked here (one device-to-host read) for every
+        new (cubes, offsets) pair; during CUDA-graph capture the check is skipped -- capture a pair
+        that has been used once outside capture."""
+        key = (cubes.data_ptr(), cubes.numel(), offsets.data_ptr(), offsets.numel())
+        if key in self._validated or self.batch == 0:
+            return
+        if torch.cuda.is_available() and torch.cuda.is_current_stream_capturing():
+            return
+        if offsets.numel() != self.batch:
+            raise ValueError(f"offsets must have {self.batch} entries")
+        off = offsets.detach().cpu().numpy()
+        if np.any(off < 0) or np.any(off + self.N > cubes.numel()):
+            raise ValueError("offsets place a cube outside the cubes buffer")
+        if len(self._validated) > 256:
+            self._validated.clear()
+        self._validated.add(key)
+
     def _bins_shape(self, n_sched):
         return (self.batch, n_sched, self.D + 1, self.L_max)
 
@@ -128,6 +149,7 @@ class Plan:
         _need(cubes, torch.complex64, "cubes")
         _need(offsets, torch.int64, "offsets")
         S = self._sched(alpha, tau)
+        self._check_extent(cubes, offsets)
         if out is None:
             out = torch.empty(self._bins_shape(S), dtype=torch.complex64, device=cubes.device)
         _need(out, torch.complex64, "out")
@@ -150,6 +172,7 @@ class Plan:
         _need(cubes, torch.complex64, "cubes")
         _need(offsets, torch.int64, "offsets")
         self._sched(alpha, tau, rows=self.T_max)
+        self._check_extent(cubes, offsets)
         if out is None:
             out = self.alloc_output(cubes.device)
         if init_count is not None:
@@ -169,6 +192,7 @@ class Plan:
             raise ValueError("host_cubes must be a contiguous pinned CPU complex64 tensor")
         _need(offsets, torch.int64, "offsets")
         self._sched(alpha, tau, rows=self.T_max)
+        self._check_extent(host_cubes, offsets)
         if out is None:
             out = self.alloc_output(offsets.device)
         _lib.check(self.lib.fpssft_recover(self.handle, _ptr(host_cubes), _ptr(offsets), _ptr(alpha), _ptr(tau),
@@ -186,6 +210,7 @@ class Plan:
             return torch.from_numpy(np.ascontiguousarray(t)).to(dtype)
         cubes = host(cubes, torch.complex64)
         offsets = host(offsets, torch.int64)
+        self._check_extent(cubes, offsets)
         alpha = host(alpha, torch.int32)
         tau = host(tau, torch.int32)
         if out is None:
@@ -198,9 +223,7 @@ class Plan:
     def synth(self, alpha, tau, k, a, count, accumulate=0, bins=None, stream=None):
         """Bins of the sparse spectrum (k, a) on the schedule lines (accumulate: 0 set, +1 add, -1 subtract)."""
         S = self._sched(alpha, tau)
-        _need(k, torch.int32, "k")
-        _need(a, torch.complex64, "a")
-        _need(count, torch.int32, "count")
+        self._check_set(k, a, count)
         if bins is None:
             bins = torch.empty(self._bins_shape(S), dtype=torch.complex64, device=a.device)
             accumulate = 0
@@ -211,10 +234,23 @@ class Plan:
 
     def decode(self, bins, alpha, tau, k, a, count, t0_count, status, stream=None):
         self._sched(alpha, tau, rows=1)
+        _need(bins, torch.complex64, "bins")
+        self._check_set(k, a, count)
+        _need(t0_count, torch.int32, "t0_count")
+        _need(status, torch.int32, "status")
         _lib.check(self.lib.fpssft_decode(self.handle, _ptr(bins), _ptr(alpha), _ptr(tau), _ptr(k), _ptr(a),
                                           _ptr(count), _ptr(t0_count), _ptr(status), _stream(stream)))
 
+    def _check_set(self, k, a, count):
+        _need(k, torch.int32, "k")
+        _need(a, torch.complex64, "a")
+        _need(count, torch.int32, "count")
+        if tuple(k.shape) != (self.batch, self.k_cap, self.D) or tuple(a.shape) != (self.batch, self.k_cap) \
+                or count.numel() != self.batch:
+            raise ValueError(f"k, a, count must be [{self.batch}][{self.k_cap}][{self.D}], [{self.batch}][{self.k_cap}], [{self.batch}]")
+
     def finalize(self, k, a, count, stream=None):
+        self._check_set(k, a, count)
         _lib.check(self.lib.fpssft_finalize(self.handle, _ptr(k), _ptr(a), _ptr(count), _stream(stream)))
 
     def adjoint_project(self, grad_bins, offsets, alpha, tau, grad_cubes, stream=None):
@@ -222,6 +258,8 @@ class Plan:
         S = self._sched(alpha, tau)
         _need(grad_bins, torch.complex64, "grad_bins")
         _need(grad_cubes, torch.complex64, "grad_cubes")
+        _need(offsets, torch.int64, "offsets")
+        self._check_extent(grad_cubes, offsets)
         _lib.check(self.lib.fpssft_adjoint(self.handle, _lib.ADJ_PROJECT, _ptr(grad_bins), _ptr(offsets),
                                            _ptr(alpha), _ptr(tau), S, None, None, _ptr(grad_cubes), _stream(stream)))
         return grad_cubes

@@ -508,3 +508,18 @@ def test_recovery_reading_cubes_in_place_from_pinned_host_memory():
         assert torch.allclose(ref.a[b, :n], got.a[b, :n], rtol=AMP_TOL, atol=0)
     with pytest.raises(ValueError):
         plan.recover_mapped(torch.from_numpy(wl.cubes), offs, al, ta)      # not pinned
+
+
+def test_offsets_that_leave_the_cube_buffer_are_rejected_before_launch():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=8)
+    plan = Plan(wl.dims, configs.params_for(wl))
+    cubes, offs, al, ta = to_dev(wl)
+    bad = offs.clone()
+    bad[-1] += 1
+    with pytest.raises(ValueError):
+        plan.recover(cubes, bad, al, ta)
+    with pytest.raises(ValueError):
+        plan.recover(cubes[:-1], offs, al, ta)
+    plan.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
