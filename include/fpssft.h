@@ -85,6 +85,8 @@ typedef struct {
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
                         FFT (every L of the batch in {32, 64, 128, 256}) */
+  int amp_average;   /* 0: amplitude from line tau only (Eq. decoding); nonzero: the mean over the
+                        D+1 lines of s_j times the conjugate of line j's offset phase (noisy data) */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;

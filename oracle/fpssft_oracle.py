@@ -48,6 +48,7 @@ class Params:
     eta: float = 0.05           # T2: |N_d phi / (2 pi) - round| <= eta
     early_stop: bool = True     # stop when no bin of line 0 passes T0 after peeling
     peel_mode: str = "bins"     # "bins" (subtract projections from the bins) or "literal"
+    amp_average: bool = False   # amplitude from line tau only (Eq. decoding) or averaged over the D+1 lines
 
 
 # ---------------------------------------------------------------------------------------------
@@ -200,6 +201,8 @@ def classify_decode(bins, alpha, tau, dims, p):
       T2  |u_d - floor(u_d + 1/2)| <= eta for every d      (the phase sits on the frequency grid)
       T3  m(k) = m                                         (Eq. orthogonality)
       a = s_0 exp(-j 2 pi sum_d k_d tau_d / N_d)            (Eq. decoding)
+    (with p.amp_average, a is the mean over the D+1 lines of s_j times the conjugate offset phase
+    of line j, an option for noisy data).
     Returns (list of (m, k tuple, a), number of bins passing T0)."""
     dims = [int(n) for n in dims]
     D = len(dims)
@@ -230,6 +233,9 @@ def classify_decode(bins, alpha, tau, dims, p):
         if int(bin_index(np.asarray(k), alpha, dims)) != int(m):
             continue
         a = s0[m] * np.conj(line_phase(np.asarray(k), tau, dims, 0))
+        if p.amp_average:
+            # every line carries the same amplitude times its own offset phase (Eq. freqSum)
+            a = sum(bins[j][m] * np.conj(line_phase(np.asarray(k), tau, dims, j)) for j in range(D + 1)) / (D + 1)
         out.append((int(m), tuple(int(v) for v in k), complex(a)))
     return out, int(np.count_nonzero(t0))
 

@@ -394,7 +394,7 @@ __device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& s
       psum += ct[d] * k[d];
     }
     if (fmod_(msum, sh.fL) != m) continue;                            // T3
-    const float2 a = cmul(s0, tw[fmod_(psum, sh.fL)]);                // a = s_0 W^-p
+    const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tw, th.amp_average != 0);
     ++my_acc;
     if (!bucket_insert<D>(s, m, k, a)) my_ovf = true;
   }
@@ -1014,6 +1014,7 @@ struct fpssft_plan_s {
     t.t1_lo_fail = lo2 > 0 ? down(lo2 * (1.0 - 2 * g)) : -1.f;
     t.eta_f = (float)t.eta;
     t.fp64_all = p.fp64_decisions ? 1 : 0;
+    t.amp_average = p.amp_average ? 1 : 0;
     return t;
   }
 };

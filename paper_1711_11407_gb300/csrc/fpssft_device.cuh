@@ -454,7 +454,26 @@ struct Thresholds {
   float t1_lo_pass, t1_lo_fail;    // e >= t1_lo_pass e0: lower T1 bound holds; e < t1_lo_fail e0: fails
   float eta_f;
   int fp64_all;
+  int amp_average;   // amplitude averaged over the D+1 lines instead of line tau only
 };
+
+// Amplitude of a decoded frequency: s_0 W^-p (Eq. decoding), or the mean over the D+1 lines of
+// s_j W^-(p + [j > 0] c_{j-1} k_{j-1}) when averaging.
+template <int D>
+__device__ __forceinline__ float2 decoded_amplitude(float2 s0, const float2* sd, const Shape& sh, const int* k, int p,
+                                                    const float2* __restrict__ tw, bool average) {
+  float2 a = cmul(s0, tw[p]);
+  if (average) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      int q = p + sh.c[d] * k[d];
+      if (q >= sh.L) q -= sh.L;
+      a = cadd(a, cmul(sd[d], tw[q]));
+    }
+    a = cscale(a, 1.0f / (float)(D + 1));
+  }
+  return a;
+}
 
 // Verdicts: 1 = every test passes (k filled), -1 = rejected, 0 = not certified in FP32.
 constexpr int kAccept = 1, kReject = -1, kUndecided = 0;
@@ -564,7 +583,7 @@ __device__ __forceinline__ void decode_bins(const float2* bins, int line_stride,
       key += k[d] * sh.strides[d];
     }
     if (fmod_(msum, sh.fL) != m) continue;                            // T3
-    const float2 a = cmul(s0, tw[fmod_(psum, sh.fL)]);                // a = s_0 W^-p
+    const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tw, th.amp_average != 0);
     if (!set_insert<D>(s, k, key, a)) my_ovf = true;
   }
   if (my_t0) atomicAdd(t0, my_t0);

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_function():
 def _plan(D, batch, dims, **kw):
     lib = _lib.load()
     p = _lib.CParams(kw.get("T", 10), kw.get("k_cap", 64), kw.get("theta0", 1e-3), 1e-3, 0.05, 1,
-                     kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0), kw.get("fft_path", 0))
+                     kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0), kw.get("fft_path", 0), 0)
     h = ctypes.c_void_p()
     d = np.ascontiguousarray(np.asarray(dims, np.int64).reshape(-1))
     st = lib.fpssft_plan_create(ctypes.byref(h), D, batch, d.ctypes.data_as(ctypes.c_void_p) if d.size else None,

@@ -523,3 +523,34 @@ def test_offsets_that_leave_the_cube_buffer_are_rejected_before_launch():
         plan.recover(cubes[:-1], offs, al, ta)
     plan.recover(cubes, offs, al, ta)
     torch.cuda.synchronize()
+
+
+def test_amplitude_averaging_matches_oracle_teacher_forced_on_noisy_data():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=4, shapes=[(64, 64)], K=lambda N: 20, T=4, snr_db=15.0)
+    p = configs.params_for(wl, T=1, k_cap=64, amp_average=True)
+    plan = Plan(wl.dims, p)
+    cubes, offs, al, ta = to_dev(wl)
+    for t in (0, 2):
+        out = plan.alloc_output()
+        init = torch.zeros(wl.batch, dtype=torch.int32, device=dev())
+        prevs = []
+        for b in range(wl.batch):
+            prev = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], O.Params(T=t, k_cap=64, theta0=p.theta0, rho=p.rho,
+                             eta=p.eta, amp_average=True), T=t) if t else None
+            prevs.append(prev)
+            if prev is not None:
+                n0 = prev.k.shape[0]
+                out.k[b, :n0] = torch.from_numpy(prev.k.astype(np.int32)).to(dev())
+                out.a[b, :n0] = torch.from_numpy(prev.a.astype(np.complex64)).to(dev())
+                init[b] = n0
+        plan.recover(cubes, offs, al[:, t:t + 1].contiguous(), ta[:, t:t + 1].contiguous(), out=out, init_count=init)
+        torch.cuda.synchronize()
+        for b in range(wl.batch):
+            pv = prevs[b]
+            nxt = O.recover(wl.cube(b), wl.alpha[b, t:t + 1], wl.tau[b, t:t + 1],
+                            O.Params(T=1, k_cap=64, theta0=p.theta0, rho=p.rho, eta=p.eta, amp_average=True),
+                            init=(pv.k, pv.a) if pv is not None else None, T=1)
+            k, a = out.signal(b)
+            assert np.array_equal(k, nxt.k), f"iteration {t} signal {b}"
+            assert np.allclose(a, nxt.a, rtol=1e-3, atol=0)
