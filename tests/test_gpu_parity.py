@@ -554,3 +554,42 @@ def test_amplitude_averaging_matches_oracle_teacher_forced_on_noisy_data():
             k, a = out.signal(b)
             assert np.array_equal(k, nxt.k), f"iteration {t} signal {b}"
             assert np.allclose(a, nxt.a, rtol=1e-3, atol=0)
+
+
+def _random_case(rng):
+    D = int(rng.integers(1, 5))
+    choices = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 20, 24, 30, 32, 64]
+    while True:
+        dims = tuple(int(rng.choice(choices)) for _ in range(D))
+        L = math.lcm(*dims)
+        N = int(np.prod(dims))
+        if L <= 2048 and N <= 65536 and N >= 4:
+            break
+    K = int(rng.integers(1, max(2, min(N // 3, L // 2)) + 1))
+    return dims, K
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_shapes_match_oracle_on_every_kernel_path(seed):
+    """Seeded random D, shapes (prime and mixed-radix line lengths), sparsity and budgets: every
+    applicable kernel path recovers exactly the oracle's set."""
+    from paper_1711_11407_gb300.api import Plan
+    from paper_1711_11407_gb300 import _lib
+    rng = np.random.default_rng(1000 + seed)
+    dims, K = _random_case(rng)
+    T = int(rng.integers(3, 16))
+    wl = small_batch([dims], 3, K=lambda N: K, T=T, seed=2000 + seed)
+    for path, gm in ((1, 1), (1, 3), (2, 1)):
+        p = configs.params_for(wl, T=T, k_cap=2 * K + 8, fft_path=path, gather_mode=gm)
+        try:
+            plan = Plan(wl.dims, p)
+        except _lib.FpssftError as e:
+            assert path == 2 and e.status == _lib.ERR_UNSUPPORTED     # register path needs L in 32..256
+            continue
+        out = plan.recover(*to_dev(wl))
+        torch.cuda.synchronize()
+        for b in range(wl.batch):
+            ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, T))
+            k, a = out.signal(b)
+            assert_same_set(k, a, ref, f"dims {dims} K {K} path {path} gather {gm} signal {b}")
+            assert int(out.iters[b]) == ref.iters and int(out.status[b]) == ref.status
