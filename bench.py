@@ -331,14 +331,15 @@ def main():
     peaks, peak_src = measured_peaks()
     achieved = useful / (ms_per_step / 1000.0) / 1e9
     traffic, _ = profiled_traffic(args.workload, wl.batch)
-    warp_path = plan.info.get("fft_path") == 2
-    kname = f"k_recover_w<{wl.D}>" if warp_path else f"k_recover<{wl.D}>"
+    path = plan.info.get("fft_path")
+    kname = {2: f"k_recover_w<{wl.D}>", 3: f"k_recover_c<{wl.D}>"}.get(path, f"k_recover<{wl.D}>")
+    kdesc = {2: "persistent; one warp per line", 3: "one CTA per line, a cluster of D+1 CTAs per signal"}.get(
+        path, "persistent; one CTA per signal")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": achieved / float(peaks["hbm_gbs"]), "traffic": traffic,
                 "peak_source": f"{peak_src} (hbm_gbs, copy bandwidth; kernel timed alone: burst figure)",
                 "algorithmic_bytes_per_launch": useful,
-                "kernel": f"{kname} (persistent; {'one warp per line' if warp_path else 'one CTA per signal'}; "
-                          "one launch per step, CUDA events on the launching stream)"}
+                "kernel": f"{kname} ({kdesc}; one launch per step, CUDA events on the launching stream)"}
     # second view: the gather against the measured random-access ceiling of this GPU.  Each line
     # position reads one adjacent pair (lines tau and tau + e_{D-1}) and D - 1 isolated samples.
     if not args.quick or args.ceiling:

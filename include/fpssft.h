@@ -84,7 +84,10 @@ typedef struct {
                         path modes 1 and 2 prefetch the next iteration into registers instead */
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
-                        FFT (every L of the batch in {32, 64, 128, 256}) */
+                        FFT (every L of the batch in {32, 64, 128, 256}), 3 = one CTA per line, the
+                        D+1 CTAs of a signal forming a thread-block cluster that exchanges bins
+                        through distributed shared memory (long lines, small batches; `threads`
+                        sets the CTA size).  Never chosen by 0 */
   int amp_average;   /* 0: amplitude from line tau only (Eq. decoding); nonzero: the mean over the
                         D+1 lines of s_j times the conjugate of line j's offset phase (noisy data) */
 } fpssft_params;
@@ -104,7 +107,8 @@ typedef struct {
   int smem_bytes;     /* dynamic shared memory per recovery CTA */
   int twiddles_in_smem;
   int prefetch;       /* 1: the next iteration's lines are gathered while the current one computes */
-  int fft_path;       /* 1: shared-memory FFT, one CTA per signal; 2: register FFT, one warp per line */
+  int fft_path;       /* 1: shared-memory FFT, one CTA per signal; 2: register FFT, one warp per line;
+                         3: one CTA per line, a cluster of D+1 CTAs per signal (grid = batch (D+1)) */
   int global_workspace; /* 1: lines and recovered set too large for shared memory live in a
                         per-CTA slice of plan-owned global workspace (fpssft_recover only) */
 } fpssft_plan_info;
@@ -151,7 +155,9 @@ fpssft_status fpssft_lines(fpssft_plan_t plan, const void* cubes, const int64_t*
  * One persistent launch processes the whole batch (longest signals first).
  *   alpha, tau:  int32 [batch][T_max][D] (device).
  *   init_count:  NULL, or int32 [batch] (device): resume from the first init_count[b] entries
- *                already present in out_k / out_a (checkpoint / teacher forcing).
+ *                already present in out_k / out_a (checkpoint / teacher forcing).  The entries
+ *                must have distinct frequencies, as fpssft_recover writes them; with repeated
+ *                frequencies the resumed set is unspecified (no access leaves the buffers).
  *   out_k, out_a, out_count: the recovered set, entries with |a| <= theta0 dropped, sorted by
  *                row-major linear frequency index.
  *   out_iters:   iterations whose lines were sampled.

@@ -1,11 +1,12 @@
 """Autotuner for the recovery launch: picks the kernel configuration of fpssft_recover for a batch.
 
 Candidates are the valid combinations of
-  fft_path     1 (one CTA per signal, shared-memory mixed-radix FFT) or 2 (one warp per line,
-               register FFT; only when every line length is 32, 64, 128 or 256),
+  fft_path     1 (one CTA per signal, shared-memory mixed-radix FFT), 2 (one warp per line,
+               register FFT; only when every line length is 32, 64, 128 or 256) or 3 (one CTA per
+               line, a cluster of D+1 CTAs per signal; only for lines of 512 points or more),
   gather_mode  1 (synchronous through L1), 2 (L2 only) or 3 (asynchronous prefetch: cp.async into
                shared memory; on path 2 it replaces the register prefetch),
-  threads      CTA size for path 1 (path 2 is fixed at 32 (D+1)).
+  threads      CTA size for paths 1 and 3 (path 2 is fixed at 32 (D+1)).
 Each candidate is timed on the caller's own inputs with CUDA events (warm-up first, a buffer larger
 than L2 written between timed launches); the fastest wins.  Results are cached in a JSON file keyed
 by GPU name, D, the sorted set of shapes, k_cap and T, so a batch with the same layout is not
@@ -49,6 +50,12 @@ def candidates(dims, params: Params):
             continue
         for gm in (1, 3):
             out.append(replace(params, fft_path=1, gather_mode=gm, threads=th))
+    if L_max >= 512:
+        for th in (256, 512, 1024):
+            if th > L_max // 2:
+                continue
+            for gm in (1, 3):
+                out.append(replace(params, fft_path=3, gather_mode=gm, threads=th))
     return out
 
 

@@ -8,6 +8,7 @@
 // the (D+1) L sample gather.  Two kernels: k_recover_w (one warp per line, register FFT, for
 // L in {32, 64, 128, 256}) and k_recover (shared-memory mixed-radix FFT, any L; with a global-
 // workspace variant for lines or sets too large for shared memory).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -595,6 +596,254 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
   }
 }
 
+// ---- cluster path: one CTA per line, the D+1 CTAs of a signal form a thread-block cluster -------
+// For long lines one CTA per signal runs the D+1 transforms one after another on one SM and leaves
+// most SMs idle when the batch is small.  Here CTA j of the signal's cluster gathers, transforms
+// and peels line j alone in its own shared memory.  Deciding bin m needs bin m of every line, so
+// each CTA decodes a (D+1)-th of the bins and reads the other lines' bins through distributed
+// shared memory.  The recovered list (k, a, key) is replicated in every CTA, so each peel reads
+// only local memory; the hash index that deduplicates keys and the entry counter are rank 0's, and
+// an insert writes the new entry into every replica.  Two cluster barriers per iteration: after
+// the peel (every line's bins final) and after the decode (every replica final).
+struct CLayout {
+  size_t bufA, bufB, bufC, tw, la, lk, lkey, hkey, hidx, total;
+};
+
+static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap, int hash_cap, bool prefetch) {
+  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
+  CLayout s{};
+  const size_t line = (size_t)L_max * sizeof(float2);
+  size_t off = 0;
+  s.bufA = off; off = al(off + line);
+  s.bufB = off; off = al(off + line);
+  s.bufC = off; off = al(off + (prefetch ? line : 0));
+  s.tw = off; off = al(off + line);
+  s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
+  s.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
+  s.lkey = off; off = al(off + (size_t)k_cap * sizeof(int));
+  s.hkey = off; off = al(off + (size_t)hash_cap * sizeof(int));
+  s.hidx = off; off = al(off + (size_t)hash_cap * sizeof(int));
+  s.total = off;
+  return s;
+}
+
+// a5 from any CTA of the cluster: hkey / hidx / count are rank 0's (generic addresses that may be
+// remote), base[r] is rank r's shared memory.  Same contract as set_insert: within one iteration
+// concurrent calls carry distinct keys, and an existing key was written in an earlier iteration
+// (made visible by the cluster barriers).  Returns false on overflow.
+template <int D>
+__device__ __forceinline__ bool cluster_insert(int* hkey, int* hidx, int* count, unsigned char* const* base,
+                                               const CLayout& lay, int k_cap, int hash_bits, int rank,
+                                               const int* k, int key, float2 a) {
+  const unsigned mask = (1u << hash_bits) - 1u;
+  unsigned h = hash_slot(key, hash_bits);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(&hkey[h], kEmpty, key);
+    if (old == kEmpty) {
+      const int idx = atomicAdd(count, 1);
+      if (idx >= k_cap) {
+        hidx[h] = -1;
+        return false;
+      }
+#pragma unroll
+      for (int r = 0; r <= D; ++r) {
+        unsigned char* p = base[r];
+        int* lk = reinterpret_cast<int*>(p + lay.lk);
+#pragma unroll
+        for (int d = 0; d < D; ++d) lk[d * k_cap + idx] = k[d];
+        reinterpret_cast<int*>(p + lay.lkey)[idx] = key;
+        reinterpret_cast<float2*>(p + lay.la)[idx] = a;
+      }
+      hidx[h] = idx;
+      return true;
+    }
+    if (old == key) {
+      const int idx = hidx[h];
+      if (idx < 0 || idx >= k_cap) return false;   // overflowed claim (or a repeated resume key)
+      // every replica holds the same value: add once, write everywhere
+      const float2 s = cadd(reinterpret_cast<const float2*>(base[rank] + lay.la)[idx], a);
+#pragma unroll
+      for (int r = 0; r <= D; ++r) reinterpret_cast<float2*>(base[r] + lay.la)[idx] = s;
+      return true;
+    }
+    h = (h + 1u) & mask;
+  }
+  return false;   // unreachable at load factor <= 1/2
+}
+
+// One signal per cluster (grid = batch clusters of D+1 CTAs, in the longest-first order).
+template <int D, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_count, s_ovf, s_n;
+  __shared__ int s_t0[2];                     // line-0 bins passing T0, by iteration parity
+  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+  __shared__ unsigned char* s_base[kMaxD + 1];  // each rank's dynamic shared memory (generic address)
+
+  const int rank = (int)cluster.block_rank();
+  const int b = A.tab.order[blockIdx.x / (D + 1)];
+  const int si = A.tab.sig_shape[b];
+  const int hash_cap = 1 << A.hash_bits;
+  const bool pf = A.prefetch != 0;
+  const CLayout lay = recover_layout_c(D, A.L_max, A.k_cap, hash_cap, pf);
+  float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
+  float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
+  float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
+  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  const float2* la = reinterpret_cast<const float2*>(smem + lay.la);
+  const int* lk = reinterpret_cast<const int*>(smem + lay.lk);
+
+  load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
+  if (threadIdx.x <= D) s_base[threadIdx.x] = cluster.map_shared_rank(smem, (int)threadIdx.x);
+  if (rank == 0) {
+    int* hk = reinterpret_cast<int*>(smem + lay.hkey);
+    for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) hk[i] = kEmpty;
+  }
+  if (threadIdx.x == 0) {
+    s_count = 0;
+    s_ovf = 0;
+    s_t0[0] = 0;
+    s_t0[1] = 0;
+  }
+  cluster.sync();   // every CTA started and initialised before any remote access
+
+  int* c_count = cluster.map_shared_rank(&s_count, 0);
+  int* c_ovf = cluster.map_shared_rank(&s_ovf, 0);
+  int* c_t0 = cluster.map_shared_rank(s_t0, 0);
+  int* c_hkey = reinterpret_cast<int*>(s_base[0] + lay.hkey);
+  int* c_hidx = reinterpret_cast<int*>(s_base[0] + lay.hidx);
+  const float2* x = A.cubes + A.offsets[b];
+  int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
+  float2* oa_out = A.out_a + (size_t)b * A.k_cap;
+
+  if (A.init_count != nullptr) {   // resume from a given set (rank 0 inserts into every replica)
+    if (rank == 0) {
+      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
+      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        int k[D];
+        int key = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          k[d] = ok_out[i * D + d];
+          key += k[d] * sh.strides[d];
+        }
+        if (on_grid<D>(sh, k) &&
+            !cluster_insert<D>(c_hkey, c_hidx, c_count, s_base, lay, A.k_cap, A.hash_bits, rank, k, key, oa_out[i]))
+          atomicOr(c_ovf, 1);
+      }
+    }
+    cluster.sync();
+  }
+  int n_set = min(*c_count, A.k_cap);
+  bool stop = *c_ovf != 0;
+
+  const int L = sh.L;
+  const int chunk = (L + D) / (D + 1);
+  const int m_lo = rank * chunk;
+  const int m_hi = min(L, m_lo + chunk);
+  const int T = stop ? 0 : A.tab.sig_T[b];
+  const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
+  const int* sched_t = A.tau + (size_t)b * A.sched_stride;
+  if (pf && T > 0) gather_one_line<D, 0, true>(bufA, x, sh, sched_a, sched_t, rank);
+  int iters = 0;
+  for (int t = 0; t < T; ++t) {
+    const int par = t & 1;
+    const int* al = sched_a + t * D;
+    const int* ta = sched_t + t * D;
+    // slot par was last read after the decode barrier of iteration t-2, before every rank
+    // arrived at the peel barrier of t-1, which this rank has passed
+    if (rank == 0 && threadIdx.x == 0) s_t0[par] = 0;
+    if (threadIdx.x < D) {
+      const int d = threadIdx.x;
+      s_ca[d] = cmodL(sh, d, al[d]);
+      s_ct[d] = cmodL(sh, d, ta[d]);
+    }
+    float2* cur = (pf && (t & 1)) ? bufC : bufA;
+    if (pf) {
+      if (t + 1 < T) {
+        gather_one_line<D, 0, true>((t & 1) ? bufA : bufC, x, sh, al + D, ta + D, rank);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else if (A.gather_mode == 2) {
+      gather_one_line<D, 1, false>(bufA, x, sh, al, ta, rank);
+    } else {
+      gather_one_line<D, 0, false>(bufA, x, sh, al, ta, rank);
+    }
+    __syncthreads();
+    float2* bins = fft_lines(cur, bufB, 1, sh, tws, 1.0f / (float)L);
+    peel_one_line<D>(bins, sh, la, lk, A.k_cap, n_set, s_ca, s_ct, tws, rank);
+    cluster.sync();   // every line peeled
+
+    const size_t boff = reinterpret_cast<unsigned char*>(bins) - smem;
+    int my_t0 = 0;
+    bool my_ovf = false;
+    for (int m = m_lo + threadIdx.x; m < m_hi; m += blockDim.x) {
+      const float2 s0 = reinterpret_cast<const float2*>(s_base[0] + boff)[m];
+      float2 sd[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) sd[d] = reinterpret_cast<const float2*>(s_base[d + 1] + boff)[m];
+      int k[D];
+      bool counted = false;
+      int v = A.th.fp64_all ? kUndecided : classify_fp32<D>(s0, sd, sh, A.th, k, &counted);
+      if (v == kUndecided) {
+        bool c64 = false;
+        v = classify_fp64<D>(s0, sd, sh, A.th, k, &c64);
+        counted = c64;
+      }
+      my_t0 += counted ? 1 : 0;
+      if (v != kAccept) continue;
+      int msum = 0, psum = 0, key = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        msum += s_ca[d] * k[d];
+        psum += s_ct[d] * k[d];
+        key += k[d] * sh.strides[d];
+      }
+      if (fmod_(msum, sh.fL) != m) continue;                            // T3
+      const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tws, A.th.amp_average != 0);
+      if (!cluster_insert<D>(c_hkey, c_hidx, c_count, s_base, lay, A.k_cap, A.hash_bits, rank, k, key, a))
+        my_ovf = true;
+    }
+    if (my_t0) atomicAdd(c_t0 + par, my_t0);
+    if (my_ovf) atomicOr(c_ovf, 1);
+    cluster.sync();   // every insert landed in every replica
+    n_set = min(*c_count, A.k_cap);
+    iters = t + 1;
+    if ((A.early_stop && c_t0[par] == 0) || *c_ovf != 0) break;   // the same verdict on every rank
+  }
+  if (pf) cp_async_wait<0>();
+  cluster.sync();   // no rank reads another's shared memory past this point
+
+  if (rank != 0) return;
+  SetView set;
+  set.la = reinterpret_cast<float2*>(smem + lay.la);
+  set.lk = reinterpret_cast<int*>(smem + lay.lk);
+  set.lkey = reinterpret_cast<int*>(smem + lay.lkey);
+  set.hkey = reinterpret_cast<int*>(smem + lay.hkey);
+  set.hidx = reinterpret_cast<int*>(smem + lay.hidx);
+  set.count = &s_count;
+  set.k_cap = A.k_cap;
+  set.hash_bits = A.hash_bits;
+  sort_kept(set, n_set, A.th, set.hkey, set.hidx, &s_n);   // hash arrays reused as sort buffers
+  const int n = s_n;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int i = set.hidx[r];
+#pragma unroll
+    for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
+    oa_out[r] = set.la[i];
+  }
+  if (threadIdx.x == 0) {
+    A.out_count[b] = n;
+    A.out_iters[b] = iters;
+    A.out_status[b] = s_ovf ? kStatusCapacity : 0;
+  }
+}
+
 // ---- projection / raw lines: one CTA per (signal, schedule row) --------------------------------
 struct ProjectArgs {
   const float2* cubes;
@@ -965,6 +1214,7 @@ struct fpssft_plan_s {
   bool prefetch = true;
   bool warp_path = false;   // k_recover_w (register FFT per line) instead of k_recover
   bool gm_path = false;     // k_recover with lines and set in global workspace
+  bool cluster_path = false;   // k_recover_c (one CTA per line, a cluster of D+1 CTAs per signal)
   bool lines_in_smem = true;   // fpssft_project / _lines / _adjoint / _synth usable
   unsigned char* d_gm_ws = nullptr;
   size_t gm_stride = 0;
@@ -1097,7 +1347,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
   if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
-  if (pr.fft_path < 0 || pr.fft_path > 2) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 2]");
+  if (pr.fft_path < 0 || pr.fft_path > 3) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 3]");
   if (pr.threads < 0 || pr.threads > 1024 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 1024]");
 
   auto* P = new (std::nothrow) fpssft_plan_s();
@@ -1222,23 +1472,51 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       return fail(FPSSFT_ERR_UNSUPPORTED, "lines + recovered set exceed one CTA's shared memory (k_cap too large)");
     }
   }
+  const bool want_pf = pr.gather_mode == 3;
+  if (pr.fft_path == 3 && batch > (1 << 28)) {
+    delete P;
+    return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 3 launches batch (D+1) CTAs: batch must be <= 2^28");
+  }
+  if (pr.fft_path == 3 && batch > 0) {
+    // one line, its FFT partner, the twiddles and a replica of the recovered list per CTA
+    CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, want_pf);
+    P->prefetch = want_pf;
+    if (cl.total + static_reserve > (size_t)optin) {
+      cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false);
+      P->prefetch = false;
+    }
+    if (cl.total + static_reserve > (size_t)optin) {
+      delete P;
+      return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 3: one line, its twiddles and the recovered set exceed one CTA's shared memory");
+    }
+    P->cluster_path = true;
+    P->tw_smem = true;
+    P->smem = cl.total;
+    if (pr.threads > 0) {
+      P->threads = pr.threads;
+    } else {
+      int t = 128;
+      while (4 * t < P->L_max && t < 1024) t <<= 1;
+      P->threads = t;
+    }
+  }
+  const bool shared_path = !P->warp_path && !P->cluster_path;
   // prefer prefetched gathers (unless a synchronous gather mode is requested) and twiddles in
   // shared memory; drop them in that order if they do not fit
-  const bool want_pf = pr.gather_mode == 3;
   SmemLayout lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, want_pf);
-  if (!P->warp_path) {
+  if (shared_path) {
     P->tw_smem = true;
     P->prefetch = want_pf;
   }
   if (lay.total + static_reserve > (size_t)optin) {
     lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, true, false);
-    if (!P->warp_path) P->prefetch = false;
+    if (shared_path) P->prefetch = false;
   }
   if (lay.total + static_reserve > (size_t)optin) {
     lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false, false);
-    if (!P->warp_path) P->tw_smem = false;
+    if (shared_path) P->tw_smem = false;
   }
-  if (!P->warp_path && lay.total + static_reserve > (size_t)optin) {
+  if (shared_path && lay.total + static_reserve > (size_t)optin) {
     // lines or set too large for shared memory: keep them in a per-CTA slice of global workspace
     P->gm_path = true;
     P->tw_smem = false;
@@ -1246,7 +1524,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     lay = recover_layout(D, P->L_max, pr.k_cap, 1 << hb, false, false);
     P->gm_stride = (lay.total + 255) & ~size_t(255);
   }
-  if (!P->warp_path) {
+  if (shared_path) {
     P->smem = P->gm_path ? 0 : lay.total;
     if (pr.threads > 0) {
       P->threads = pr.threads;
@@ -1287,16 +1565,35 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     constexpr int DD = decltype(Dc)::value;
     if (P->gm_path) P->threads = std::min(P->threads, 512);
     const void* kfn = P->warp_path ? (P->prefetch ? (const void*)k_recover_w<DD, true> : (const void*)k_recover_w<DD, false>)
+                    : P->cluster_path ? (P->threads > 512 ? (const void*)k_recover_c<DD, 1024> : (const void*)k_recover_c<DD, 512>)
                     : P->gm_path ? (const void*)k_recover<DD, 512, true>
                     : (P->threads > 512 ? (const void*)k_recover<DD, 1024> : (const void*)k_recover<DD, 512>);
     cudaError_t e2 = ensure_dynamic_smem(kfn, P->smem);
     if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
+    if (P->cluster_path) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = DD + 1;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(batch * (DD + 1)));
+      cfg.blockDim = dim3((unsigned)P->threads);
+      cfg.dynamicSmemBytes = P->smem;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      e2 = cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg);
+      if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cluster occupancy query: ") + cudaGetErrorString(e2));
+      if (clusters < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "a cluster of D+1 recovery CTAs cannot be resident with this CTA size / shared memory");
+    }
     int per_sm = 0;
     e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, P->threads, P->smem);
     if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e2));
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
     P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
+    if (P->cluster_path) P->grid = batch * (DD + 1);   // one cluster per signal, not persistent
     if (P->gm_path) {   // cap the persistent grid: every CTA owns a workspace slice
       P->grid = std::max(1, std::min(batch, 2 * P->sm_count));
       const size_t bytes = (size_t)P->grid * P->gm_stride;
@@ -1351,7 +1648,7 @@ extern "C" fpssft_status fpssft_plan_get_info(fpssft_plan_t P, fpssft_plan_info*
   info->smem_bytes = (int)P->smem;
   info->twiddles_in_smem = P->tw_smem ? 1 : 0;
   info->prefetch = P->prefetch ? 1 : 0;
-  info->fft_path = P->warp_path ? 2 : 1;
+  info->fft_path = P->cluster_path ? 3 : P->warp_path ? 2 : 1;
   info->global_workspace = P->gm_path ? 1 : 0;
   return FPSSFT_OK;
 }
@@ -1457,6 +1754,23 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
         k_recover_w<DD, true><<<P->grid, P->threads, P->smem, s>>>(A);
       else
         k_recover_w<DD, false><<<P->grid, P->threads, P->smem, s>>>(A);
+    } else if (P->cluster_path) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = DD + 1;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)P->grid);
+      cfg.blockDim = dim3((unsigned)P->threads);
+      cfg.dynamicSmemBytes = P->smem;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (P->threads > 512)
+        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 1024>, A));
+      else
+        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 512>, A));
     } else if (P->gm_path) {
       k_recover<DD, 512, true><<<P->grid, P->threads, 0, s>>>(A);
     } else if (P->threads > 512) {

@@ -178,6 +178,28 @@ __device__ __forceinline__ int line_address(const Shape& sh, const int* al, cons
   return base;
 }
 
+// Line j alone into buf[0, L) (one CTA per line): synchronous (LM as in load_sample) or, ASYNC,
+// as cp.async copies committed as one group.
+template <int D, int LM, bool ASYNC>
+__device__ __forceinline__ void gather_one_line(float2* __restrict__ buf, const float2* __restrict__ x,
+                                                const Shape& sh, const int* __restrict__ alpha,
+                                                const int* __restrict__ tau, int j) {
+  int al[D], ta[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    al[d] = fmod_(__ldg(alpha + d) & 0x3fffffff, sh.fdims[d]);
+    ta[d] = fmod_(__ldg(tau + d) & 0x3fffffff, sh.fdims[d]);
+  }
+  for (int l = threadIdx.x; l < sh.L; l += blockDim.x) {
+    const float2* src = x + line_address<D>(sh, al, ta, j, l);
+    if (ASYNC)
+      cp_async8(buf + l, src);
+    else
+      buf[l] = load_sample<LM>(src);
+  }
+  if (ASYNC) cp_async_commit();
+}
+
 // ------------------------------------------------------------------------------------------------
 // a2: L-point DFT of every line (Eq. hs), mixed-radix Stockham in shared memory
 // ------------------------------------------------------------------------------------------------
@@ -383,7 +405,7 @@ __device__ __forceinline__ bool set_insert(const SetView& s, const int* k, int k
     }
     if (old == key) {
       const int idx = s.hidx[h];
-      if (idx < 0) return false;
+      if (idx < 0 || idx >= s.k_cap) return false;   // overflowed claim (or a repeated resume key)
       s.la[idx] = cadd(s.la[idx], a);
       return true;
     }
@@ -432,6 +454,30 @@ __device__ __forceinline__ void peel_set(float2* bins, const Shape& sh, const Se
 #pragma unroll
     for (int d = 0; d < D; ++d) k[d] = s.lk[d * s.k_cap + i];
     project_entry<D>(bins, sh.L, sh, k, s.la[i], ca, ct, tw, -1.f);
+  }
+}
+
+// The same peel for line j alone: entry i lands in bin m with phase p (j = 0) or p + c_{j-1} k_{j-1}.
+template <int D>
+__device__ __forceinline__ void peel_one_line(float2* bins, const Shape& sh, const float2* la, const int* lk,
+                                              int k_cap, int count, const int* ca, const int* ct,
+                                              const float2* __restrict__ tw, int j) {
+  const int L = sh.L;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int msum = 0, psum = 0, shift = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int k = lk[d * k_cap + i];
+      msum += ca[d] * k;
+      psum += ct[d] * k;
+      if (d == j - 1) shift = sh.c[d] * k;
+    }
+    const int m = fmod_(msum, sh.fL);
+    int q = fmod_(psum, sh.fL) + shift;
+    if (q >= L) q -= L;
+    const float2 v = cmulc(la[i], tw[q]);
+    atomicAdd(&bins[m].x, -v.x);
+    atomicAdd(&bins[m].y, -v.y);
   }
 }
 

@@ -52,7 +52,7 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"threads": 2048}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
     (2, 1, [8, 8], {"gather_mode": 4}, _lib.ERR_INVALID),
-    (2, 1, [8, 8], {"fft_path": 3}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"fft_path": 4}, _lib.ERR_INVALID),
     (2, 1, [1 << 20, 3], {}, _lib.ERR_UNSUPPORTED),         # D L max N_d >= 2^31
     (2, 1, [65536, 65536], {}, _lib.ERR_UNSUPPORTED),       # N >= 2^31
 ])

@@ -579,7 +579,7 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
     dims, K = _random_case(rng)
     T = int(rng.integers(3, 16))
     wl = small_batch([dims], 3, K=lambda N: K, T=T, seed=2000 + seed)
-    for path, gm in ((1, 1), (1, 3), (2, 1)):
+    for path, gm in ((1, 1), (1, 3), (2, 1), (3, 1), (3, 3)):
         p = configs.params_for(wl, T=T, k_cap=2 * K + 8, fft_path=path, gather_mode=gm)
         try:
             plan = Plan(wl.dims, p)
