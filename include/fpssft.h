@@ -78,16 +78,18 @@ typedef struct {
                         FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a
                         guard band around a threshold -- the verdicts are the same either way */
   int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice (synchronous
-                        through L1), 1 = synchronous through L1, 2 = synchronous cached in L2 only,
-                        3 = asynchronous copies (cp.async) of the next iteration's lines into a
-                        shared-memory buffer while the current one computes.  On the register-FFT
-                        path modes 1 and 2 prefetch the next iteration into registers instead */
+                        through L1 on paths 1 and 2, mode 3 on path 3), 1 = synchronous through L1,
+                        2 = synchronous cached in L2 only, 3 = asynchronous copies (cp.async) of the
+                        next iteration's lines into a shared-memory buffer while the current one
+                        computes.  On the register-FFT path modes 1 and 2 prefetch the next
+                        iteration into registers instead */
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
                         FFT (every L of the batch in {32, 64, 128, 256}), 3 = one CTA per line, the
                         D+1 CTAs of a signal forming a thread-block cluster that exchanges bins
-                        through distributed shared memory (long lines, small batches; `threads`
-                        sets the CTA size).  Never chosen by 0 */
+                        through distributed shared memory (`threads` sets the CTA size).  0 picks
+                        2 when it applies, else 3 when L_max >= 1024, batch <= 2 x SM count and
+                        one line plus the set fit one CTA's shared memory, else 1 */
   int amp_average;   /* 0: amplitude from line tau only (Eq. decoding); nonzero: the mean over the
                         D+1 lines of s_j times the conjugate of line j's offset phase (noisy data) */
 } fpssft_params;

@@ -601,74 +601,120 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
 // most SMs idle when the batch is small.  Here CTA j of the signal's cluster gathers, transforms
 // and peels line j alone in its own shared memory.  Deciding bin m needs bin m of every line, so
 // each CTA decodes a (D+1)-th of the bins and reads the other lines' bins through distributed
-// shared memory.  The recovered list (k, a, key) is replicated in every CTA, so each peel reads
-// only local memory; the hash index that deduplicates keys and the entry counter are rank 0's, and
-// an insert writes the new entry into every replica.  Two cluster barriers per iteration: after
-// the peel (every line's bins final) and after the decode (every replica final).
+// shared memory.  The recovered list (key, a) is replicated in every CTA, so each peel reads only
+// local memory (k is recovered from the row-major key); the open-addressing index that
+// deduplicates keys is split into D+1 contiguous slices, one per rank, and the entry counter is
+// rank 0's.  An insert claims its slot wherever it lies and writes the entry into every replica.
+// Two cluster barriers per iteration: after the peel (every line's bins final) and after the
+// decode (every replica final).  Per CTA: one line, its FFT partner, the prefetch buffer, the
+// twiddles, 12 bytes per set entry and 8 bytes per index slot / (D+1).
 struct CLayout {
-  size_t bufA, bufB, bufC, tw, la, lk, lkey, hkey, hidx, total;
+  size_t bufA, bufB, bufC, tw, sort, la, lkey, hkey, hidx, total;
+  int hc;   // index slots per rank
 };
 
 static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap, int hash_cap, bool prefetch) {
   auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
   CLayout s{};
   const size_t line = (size_t)L_max * sizeof(float2);
+  size_t P = 1;
+  while (P < (size_t)k_cap) P <<= 1;
+  s.hc = (hash_cap + D) / (D + 1);
   size_t off = 0;
   s.bufA = off; off = al(off + line);
   s.bufB = off; off = al(off + line);
   s.bufC = off; off = al(off + (prefetch ? line : 0));
   s.tw = off; off = al(off + line);
+  // the output sort (rank 0, after the last barrier) reuses the line buffers: 2 P ints
+  s.sort = 0;
+  const size_t sort_bytes = al(2 * P * sizeof(int));
+  if (off < sort_bytes) off = sort_bytes;
   s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
-  s.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
   s.lkey = off; off = al(off + (size_t)k_cap * sizeof(int));
-  s.hkey = off; off = al(off + (size_t)hash_cap * sizeof(int));
-  s.hidx = off; off = al(off + (size_t)hash_cap * sizeof(int));
+  s.hkey = off; off = al(off + (size_t)s.hc * sizeof(int));
+  s.hidx = off; off = al(off + (size_t)s.hc * sizeof(int));
   s.total = off;
   return s;
 }
 
-// a5 from any CTA of the cluster: hkey / hidx / count are rank 0's (generic addresses that may be
-// remote), base[r] is rank r's shared memory.  Same contract as set_insert: within one iteration
+// Frequency components of a row-major linear index (key < N).
+template <int D>
+__device__ __forceinline__ void key_to_k(const Shape& sh, int key, int* k) {
+#pragma unroll
+  for (int d = D - 1; d >= 0; --d) {
+    const int q = fdiv(key, sh.fdims[d]);
+    k[d] = key - q * sh.dims[d];
+    key = q;
+  }
+}
+
+// a5 from any CTA of the cluster: index slot h lives in rank h / hc at h mod hc, the counter is
+// rank 0's, base[r] is rank r's shared memory.  Same contract as set_insert: within one iteration
 // concurrent calls carry distinct keys, and an existing key was written in an earlier iteration
 // (made visible by the cluster barriers).  Returns false on overflow.
 template <int D>
-__device__ __forceinline__ bool cluster_insert(int* hkey, int* hidx, int* count, unsigned char* const* base,
-                                               const CLayout& lay, int k_cap, int hash_bits, int rank,
-                                               const int* k, int key, float2 a) {
+__device__ __forceinline__ bool cluster_insert(unsigned char* const* base, const CLayout& lay, int* count, int k_cap,
+                                               int hash_bits, int rank, int key, float2 a) {
   const unsigned mask = (1u << hash_bits) - 1u;
   unsigned h = hash_slot(key, hash_bits);
   for (unsigned probe = 0; probe <= mask; ++probe) {
-    const int old = atomicCAS(&hkey[h], kEmpty, key);
+    const int r = (int)(h / (unsigned)lay.hc);
+    const int i = (int)(h - (unsigned)r * (unsigned)lay.hc);
+    int* hkey = reinterpret_cast<int*>(base[r] + lay.hkey);
+    int* hidx = reinterpret_cast<int*>(base[r] + lay.hidx);
+    const int old = atomicCAS(&hkey[i], kEmpty, key);
     if (old == kEmpty) {
       const int idx = atomicAdd(count, 1);
       if (idx >= k_cap) {
-        hidx[h] = -1;
+        hidx[i] = -1;
         return false;
       }
 #pragma unroll
-      for (int r = 0; r <= D; ++r) {
-        unsigned char* p = base[r];
-        int* lk = reinterpret_cast<int*>(p + lay.lk);
-#pragma unroll
-        for (int d = 0; d < D; ++d) lk[d * k_cap + idx] = k[d];
-        reinterpret_cast<int*>(p + lay.lkey)[idx] = key;
-        reinterpret_cast<float2*>(p + lay.la)[idx] = a;
+      for (int q = 0; q <= D; ++q) {
+        reinterpret_cast<int*>(base[q] + lay.lkey)[idx] = key;
+        reinterpret_cast<float2*>(base[q] + lay.la)[idx] = a;
       }
-      hidx[h] = idx;
+      hidx[i] = idx;
       return true;
     }
     if (old == key) {
-      const int idx = hidx[h];
+      const int idx = hidx[i];
       if (idx < 0 || idx >= k_cap) return false;   // overflowed claim (or a repeated resume key)
       // every replica holds the same value: add once, write everywhere
       const float2 s = cadd(reinterpret_cast<const float2*>(base[rank] + lay.la)[idx], a);
 #pragma unroll
-      for (int r = 0; r <= D; ++r) reinterpret_cast<float2*>(base[r] + lay.la)[idx] = s;
+      for (int q = 0; q <= D; ++q) reinterpret_cast<float2*>(base[q] + lay.la)[idx] = s;
       return true;
     }
     h = (h + 1u) & mask;
   }
   return false;   // unreachable at load factor <= 1/2
+}
+
+// Peel of line j from the (key, a) list: entry i lands in bin m with phase p (j = 0) or
+// p + c_{j-1} k_{j-1}.
+template <int D>
+__device__ __forceinline__ void peel_line_keys(float2* bins, const Shape& sh, const float2* la, const int* lkey,
+                                               int count, const int* ca, const int* ct,
+                                               const float2* __restrict__ tw, int j) {
+  const int L = sh.L;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int k[D];
+    key_to_k<D>(sh, lkey[i], k);
+    int msum = 0, psum = 0, shift = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      msum += ca[d] * k[d];
+      psum += ct[d] * k[d];
+      if (d == j - 1) shift = sh.c[d] * k[d];
+    }
+    const int m = fmod_(msum, sh.fL);
+    int q = fmod_(psum, sh.fL) + shift;
+    if (q >= L) q -= L;
+    const float2 v = cmulc(la[i], tw[q]);
+    atomicAdd(&bins[m].x, -v.x);
+    atomicAdd(&bins[m].y, -v.y);
+  }
 }
 
 // One signal per cluster (grid = batch clusters of D+1 CTAs, in the longest-first order).
@@ -686,21 +732,20 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   const int rank = (int)cluster.block_rank();
   const int b = A.tab.order[blockIdx.x / (D + 1)];
   const int si = A.tab.sig_shape[b];
-  const int hash_cap = 1 << A.hash_bits;
   const bool pf = A.prefetch != 0;
-  const CLayout lay = recover_layout_c(D, A.L_max, A.k_cap, hash_cap, pf);
+  const CLayout lay = recover_layout_c(D, A.L_max, A.k_cap, 1 << A.hash_bits, pf);
   float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
   float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
   float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
   const float2* la = reinterpret_cast<const float2*>(smem + lay.la);
-  const int* lk = reinterpret_cast<const int*>(smem + lay.lk);
+  const int* lkey = reinterpret_cast<const int*>(smem + lay.lkey);
 
   load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
   if (threadIdx.x <= D) s_base[threadIdx.x] = cluster.map_shared_rank(smem, (int)threadIdx.x);
-  if (rank == 0) {
+  {
     int* hk = reinterpret_cast<int*>(smem + lay.hkey);
-    for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) hk[i] = kEmpty;
+    for (int i = threadIdx.x; i < lay.hc; i += blockDim.x) hk[i] = kEmpty;
   }
   if (threadIdx.x == 0) {
     s_count = 0;
@@ -713,8 +758,6 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   int* c_count = cluster.map_shared_rank(&s_count, 0);
   int* c_ovf = cluster.map_shared_rank(&s_ovf, 0);
   int* c_t0 = cluster.map_shared_rank(s_t0, 0);
-  int* c_hkey = reinterpret_cast<int*>(s_base[0] + lay.hkey);
-  int* c_hidx = reinterpret_cast<int*>(s_base[0] + lay.hidx);
   const float2* x = A.cubes + A.offsets[b];
   int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
   float2* oa_out = A.out_a + (size_t)b * A.k_cap;
@@ -730,15 +773,14 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
           k[d] = ok_out[i * D + d];
           key += k[d] * sh.strides[d];
         }
-        if (on_grid<D>(sh, k) &&
-            !cluster_insert<D>(c_hkey, c_hidx, c_count, s_base, lay, A.k_cap, A.hash_bits, rank, k, key, oa_out[i]))
+        if (on_grid<D>(sh, k) && !cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, oa_out[i]))
           atomicOr(c_ovf, 1);
       }
     }
     cluster.sync();
   }
   int n_set = min(*c_count, A.k_cap);
-  bool stop = *c_ovf != 0;
+  const bool stop = *c_ovf != 0;
 
   const int L = sh.L;
   const int chunk = (L + D) / (D + 1);
@@ -776,7 +818,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     }
     __syncthreads();
     float2* bins = fft_lines(cur, bufB, 1, sh, tws, 1.0f / (float)L);
-    peel_one_line<D>(bins, sh, la, lk, A.k_cap, n_set, s_ca, s_ct, tws, rank);
+    peel_line_keys<D>(bins, sh, la, lkey, n_set, s_ca, s_ct, tws, rank);
     cluster.sync();   // every line peeled
 
     const size_t boff = reinterpret_cast<unsigned char*>(bins) - smem;
@@ -806,8 +848,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
       }
       if (fmod_(msum, sh.fL) != m) continue;                            // T3
       const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tws, A.th.amp_average != 0);
-      if (!cluster_insert<D>(c_hkey, c_hidx, c_count, s_base, lay, A.k_cap, A.hash_bits, rank, k, key, a))
-        my_ovf = true;
+      if (!cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, a)) my_ovf = true;
     }
     if (my_t0) atomicAdd(c_t0 + par, my_t0);
     if (my_ovf) atomicOr(c_ovf, 1);
@@ -820,21 +861,22 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   cluster.sync();   // no rank reads another's shared memory past this point
 
   if (rank != 0) return;
-  SetView set;
+  SetView set{};
   set.la = reinterpret_cast<float2*>(smem + lay.la);
-  set.lk = reinterpret_cast<int*>(smem + lay.lk);
   set.lkey = reinterpret_cast<int*>(smem + lay.lkey);
-  set.hkey = reinterpret_cast<int*>(smem + lay.hkey);
-  set.hidx = reinterpret_cast<int*>(smem + lay.hidx);
-  set.count = &s_count;
   set.k_cap = A.k_cap;
-  set.hash_bits = A.hash_bits;
-  sort_kept(set, n_set, A.th, set.hkey, set.hidx, &s_n);   // hash arrays reused as sort buffers
+  int P = 1;
+  while (P < A.k_cap) P <<= 1;
+  int* skey = reinterpret_cast<int*>(smem + lay.sort);   // the line buffers, free now
+  int* sidx = skey + P;
+  sort_kept(set, n_set, A.th, skey, sidx, &s_n);
   const int n = s_n;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int i = set.hidx[r];
+    const int i = sidx[r];
+    int k[D];
+    key_to_k<D>(sh, set.lkey[i], k);
 #pragma unroll
-    for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
+    for (int d = 0; d < D; ++d) ok_out[r * D + d] = k[d];
     oa_out[r] = set.la[i];
   }
   if (threadIdx.x == 0) {
@@ -1477,10 +1519,16 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     delete P;
     return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 3 launches batch (D+1) CTAs: batch must be <= 2^28");
   }
-  if (pr.fft_path == 3 && batch > 0) {
-    // one line, its FFT partner, the twiddles and a replica of the recovered list per CTA
-    CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, want_pf);
-    P->prefetch = want_pf;
+  // library choice: long lines and no more signals than twice the SM count go to the cluster
+  // path when it fits (one CTA per signal would leave SMs idle and run the lines one by one)
+  const bool cluster_auto = pr.fft_path == 0 && !P->warp_path && P->L_max >= 1024 && batch <= 2 * sms &&
+                            recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false).total + static_reserve <= (size_t)optin;
+  if ((pr.fft_path == 3 || cluster_auto) && batch > 0) {
+    // one line, its FFT partner, the twiddles and a replica of the recovered list per CTA; the
+    // next iteration's line is prefetched unless a synchronous gather mode is requested
+    const bool pf_c = pr.gather_mode == 0 || pr.gather_mode == 3;
+    CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c);
+    P->prefetch = pf_c;
     if (cl.total + static_reserve > (size_t)optin) {
       cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false);
       P->prefetch = false;
@@ -1496,7 +1544,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       P->threads = pr.threads;
     } else {
       int t = 128;
-      while (4 * t < P->L_max && t < 1024) t <<= 1;
+      while (2 * t < P->L_max && t < 512) t <<= 1;
       P->threads = t;
     }
   }

@@ -457,30 +457,6 @@ __device__ __forceinline__ void peel_set(float2* bins, const Shape& sh, const Se
   }
 }
 
-// The same peel for line j alone: entry i lands in bin m with phase p (j = 0) or p + c_{j-1} k_{j-1}.
-template <int D>
-__device__ __forceinline__ void peel_one_line(float2* bins, const Shape& sh, const float2* la, const int* lk,
-                                              int k_cap, int count, const int* ca, const int* ct,
-                                              const float2* __restrict__ tw, int j) {
-  const int L = sh.L;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    int msum = 0, psum = 0, shift = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int k = lk[d * k_cap + i];
-      msum += ca[d] * k;
-      psum += ct[d] * k;
-      if (d == j - 1) shift = sh.c[d] * k;
-    }
-    const int m = fmod_(msum, sh.fL);
-    int q = fmod_(psum, sh.fL) + shift;
-    if (q >= L) q -= L;
-    const float2 v = cmulc(la[i], tw[q]);
-    atomicAdd(&bins[m].x, -v.x);
-    atomicAdd(&bins[m].y, -v.y);
-  }
-}
-
 // ------------------------------------------------------------------------------------------------
 // a4 + a5: 1-sparsity tests, OFDM-trick decode (Eq. decoding) and merge
 // ------------------------------------------------------------------------------------------------
