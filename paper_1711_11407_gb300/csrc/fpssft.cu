@@ -420,7 +420,7 @@ __device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh,
     }
   }
   __syncthreads();
-  bitonic_sort_pairs(skey, sidx, *n_out);
+  sort_pairs(skey, sidx, *n_out);
 }
 
 // When every bin that passed T0 in iteration t-1 was decoded and merged, the set is most likely

@@ -656,6 +656,60 @@ __device__ __forceinline__ void bitonic_sort_pairs(int* skey, int* sidx, int n) 
   }
 }
 
+// Rank sort for n <= 4 blockDim unique keys: the final position of a key is the number of smaller
+// keys.  Thread t owns positions t + q blockDim (q < E) and counts over the whole key array with
+// broadcast shared-memory reads (16 bytes at a time when skey is 16-byte aligned), so the count
+// needs no barrier; the permuted pairs are written back after one.
+template <int E>
+__device__ __forceinline__ void rank_sort_pairs(int* skey, int* sidx, int n) {
+  int mk[E], mi[E], rk[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int p = threadIdx.x + q * blockDim.x;
+    mk[q] = p < n ? skey[p] : 0x7fffffff;
+    mi[q] = p < n ? sidx[p] : -1;
+    rk[q] = 0;
+  }
+  if ((int)threadIdx.x < n) {
+    int j = 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(skey) & 15) == 0;
+    for (; vec && j + 4 <= n; j += 4) {
+      const int4 v = *reinterpret_cast<const int4*>(skey + j);
+#pragma unroll
+      for (int q = 0; q < E; ++q)
+        rk[q] += (v.x < mk[q] ? 1 : 0) + (v.y < mk[q] ? 1 : 0) + (v.z < mk[q] ? 1 : 0) + (v.w < mk[q] ? 1 : 0);
+    }
+    for (; j < n; ++j) {
+      const int v = skey[j];
+#pragma unroll
+      for (int q = 0; q < E; ++q) rk[q] += v < mk[q] ? 1 : 0;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    if (threadIdx.x + q * blockDim.x < n) {
+      skey[rk[q]] = mk[q];
+      sidx[rk[q]] = mi[q];
+    }
+  }
+  __syncthreads();
+}
+
+// Sort n (skey, sidx) pairs with unique keys by key; the caller has synchronised after writing
+// them.  Up to 4 blockDim pairs by rank, more by the bitonic network (pow2ceil(n) entries).
+__device__ __forceinline__ void sort_pairs(int* skey, int* sidx, int n) {
+  const int E = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  switch (E) {
+    case 0: return;
+    case 1: rank_sort_pairs<1>(skey, sidx, n); return;
+    case 2: rank_sort_pairs<2>(skey, sidx, n); return;
+    case 3: rank_sort_pairs<3>(skey, sidx, n); return;
+    case 4: rank_sort_pairs<4>(skey, sidx, n); return;
+    default: bitonic_sort_pairs(skey, sidx, n); return;
+  }
+}
+
 // Compact the entries with |a| > theta0 into (skey, sidx) and sort them by linear index: on return
 // *n_out is the number kept and sidx[r] the list position of the r-th smallest key.
 __device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thresholds& th, int* skey, int* sidx,
@@ -670,7 +724,7 @@ __device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thr
     }
   }
   __syncthreads();
-  bitonic_sort_pairs(skey, sidx, *n_out);
+  sort_pairs(skey, sidx, *n_out);
 }
 
 }  // namespace fpssft
