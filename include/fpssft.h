@@ -194,12 +194,15 @@ fpssft_status fpssft_synth(fpssft_plan_t plan, const int32_t* alpha, const int32
 /* One iteration's classification, decode and merge on precomputed bins [batch][1][D+1][L_max]
  * (already peeled), updating the set (k, a, count) in place, as in fpssft_recover.  Writes the
  * number of line-0 bins passing T0 to t0_count [batch] and ORs FPSSFT_ERR_CAPACITY into status.
- * Building block of the unfused, per-iteration host-driven form of the loop. */
+ * Building block of the unfused, per-iteration host-driven form of the loop.  Returns
+ * FPSSFT_ERR_UNSUPPORTED (nothing launched) when one signal's set (k_cap entries and index) does
+ * not fit one CTA's shared memory. */
 fpssft_status fpssft_decode(fpssft_plan_t plan, const void* bins, const int32_t* alpha,
                             const int32_t* tau, int32_t* k, void* a, int32_t* count,
                             int32_t* t0_count, int32_t* status, void* stream);
 
-/* Drop entries with |a| <= theta0 and sort each signal's set by linear index (in place). */
+/* Drop entries with |a| <= theta0 and sort each signal's set by linear index (in place).
+ * FPSSFT_ERR_UNSUPPORTED as for fpssft_decode. */
 fpssft_status fpssft_finalize(fpssft_plan_t plan, int32_t* k, void* a, int32_t* count, void* stream);
 
 typedef enum { FPSSFT_ADJ_PROJECT = 0, FPSSFT_ADJ_SYNTH = 1 } fpssft_adj_mode;

@@ -1258,6 +1258,7 @@ struct fpssft_plan_s {
   bool gm_path = false;     // k_recover with lines and set in global workspace
   bool cluster_path = false;   // k_recover_c (one CTA per line, a cluster of D+1 CTAs per signal)
   bool lines_in_smem = true;   // fpssft_project / _lines / _adjoint / _synth usable
+  bool set_in_smem = true;     // fpssft_decode / _finalize usable (one signal's set in one CTA)
   unsigned char* d_gm_ws = nullptr;
   size_t gm_stride = 0;
   size_t smem = 0;
@@ -1656,8 +1657,9 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       if (e2 == cudaSuccess) e2 = ensure_dynamic_smem((const void*)k_synth<DD>, ls / 2);
     }
     const size_t ds = (size_t)P->p.k_cap * (sizeof(float2) + (DD + 1) * sizeof(int)) + (size_t)2 * (1 << P->hash_bits) * sizeof(int);
-    if (e2 == cudaSuccess && ds <= (size_t)optin) e2 = ensure_dynamic_smem((const void*)k_decode<DD>, ds);
-    if (e2 == cudaSuccess && ds <= (size_t)optin) e2 = ensure_dynamic_smem((const void*)k_finalize<DD>, ds);
+    P->set_in_smem = ds + sizeof(Shape) + 256 <= (size_t)optin;
+    if (e2 == cudaSuccess && P->set_in_smem) e2 = ensure_dynamic_smem((const void*)k_decode<DD>, ds);
+    if (e2 == cudaSuccess && P->set_in_smem) e2 = ensure_dynamic_smem((const void*)k_finalize<DD>, ds);
     if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e2));
     return FPSSFT_OK;
   });
@@ -1932,6 +1934,7 @@ extern "C" fpssft_status fpssft_decode(fpssft_plan_t P, const void* bins, const 
   if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
   if (P->batch == 0) return FPSSFT_OK;
   if (!bins || !alpha || !tau || !k || !a || !count || !t0_count || !status) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  if (!P->set_in_smem) return fail(FPSSFT_ERR_UNSUPPORTED, "fpssft_decode keeps one signal's set in one CTA's shared memory: k_cap too large");
   DecodeArgs A;
   A.bins = static_cast<const float2*>(bins);
   A.alpha = alpha;
@@ -1960,6 +1963,7 @@ extern "C" fpssft_status fpssft_finalize(fpssft_plan_t P, int32_t* k, void* a, i
   if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
   if (P->batch == 0) return FPSSFT_OK;
   if (!k || !a || !count) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  if (!P->set_in_smem) return fail(FPSSFT_ERR_UNSUPPORTED, "fpssft_finalize keeps one signal's set in one CTA's shared memory: k_cap too large");
   FinalizeArgs A;
   A.tab = P->tables();
   A.batch = P->batch;

@@ -480,21 +480,39 @@ struct Thresholds {
 };
 
 // Amplitude of a decoded frequency: s_0 W^-p (Eq. decoding), or the mean over the D+1 lines of
-// s_j W^-(p + [j > 0] c_{j-1} k_{j-1}) when averaging.
+// s_j W^-(p + [j > 0] c_{j-1} k_{j-1}) when averaging.  The average is out of line (its operands
+// passed by value) so that the option costs the recovery loops no registers when it is off.
+template <int D>
+struct BinOperands {
+  float2 sd[D];
+  int k[D];
+};
+
+template <int D>
+__device__ __noinline__ float2 averaged_amplitude(float2 a0, BinOperands<D> v, const Shape& sh, int p,
+                                                  const float2* __restrict__ tw) {
+  float2 a = a0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int q = p + sh.c[d] * v.k[d];
+    if (q >= sh.L) q -= sh.L;
+    a = cadd(a, cmul(v.sd[d], tw[q]));
+  }
+  return cscale(a, 1.0f / (float)(D + 1));
+}
+
 template <int D>
 __device__ __forceinline__ float2 decoded_amplitude(float2 s0, const float2* sd, const Shape& sh, const int* k, int p,
                                                     const float2* __restrict__ tw, bool average) {
-  float2 a = cmul(s0, tw[p]);
-  if (average) {
+  const float2 a = cmul(s0, tw[p]);
+  if (!average) return a;
+  BinOperands<D> v;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      int q = p + sh.c[d] * k[d];
-      if (q >= sh.L) q -= sh.L;
-      a = cadd(a, cmul(sd[d], tw[q]));
-    }
-    a = cscale(a, 1.0f / (float)(D + 1));
+  for (int d = 0; d < D; ++d) {
+    v.sd[d] = sd[d];
+    v.k[d] = k[d];
   }
-  return a;
+  return averaged_amplitude<D>(a, v, sh, p, tw);
 }
 
 // Verdicts: 1 = every test passes (k filled), -1 = rejected, 0 = not certified in FP32.

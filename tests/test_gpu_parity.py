@@ -461,6 +461,31 @@ def test_long_lines_and_large_sets_use_global_workspace_and_match_oracle():
             assert int(out.iters[b]) == ref.iters
 
 
+def test_unfused_steps_reject_sets_larger_than_shared_memory():
+    """fpssft_decode / fpssft_finalize keep one signal's set in one CTA: with k_cap = 20000 they
+    return FPSSFT_ERR_UNSUPPORTED before launching anything, and the fused recovery still works."""
+    from paper_1711_11407_gb300 import _lib
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("sparse_image_512x576", batch=1)
+    plan = Plan(wl.dims, configs.params_for(wl, k_cap=20000, T=1))
+    D, d = wl.D, dev()
+    k = torch.zeros((1, plan.k_cap, D), dtype=torch.int32, device=d)
+    a = torch.zeros((1, plan.k_cap), dtype=torch.complex64, device=d)
+    count = torch.zeros(1, dtype=torch.int32, device=d)
+    t0 = torch.zeros(1, dtype=torch.int32, device=d)
+    status = torch.zeros(1, dtype=torch.int32, device=d)
+    al = torch.from_numpy(wl.alpha[:, :1]).to(d).contiguous()
+    ta = torch.from_numpy(wl.tau[:, :1]).to(d).contiguous()
+    bins = torch.zeros((1, 1, D + 1, plan.L_max), dtype=torch.complex64, device=d)
+    for call in (lambda: plan.decode(bins, al, ta, k, a, count, t0, status), lambda: plan.finalize(k, a, count)):
+        with pytest.raises(_lib.FpssftError) as e:
+            call()
+        assert e.value.status == _lib.ERR_UNSUPPORTED
+    out = plan.recover(*to_dev(wl))
+    torch.cuda.synchronize()
+    assert int(out.status[0]) == 0 and int(out.iters[0]) == 1
+
+
 def test_axis_schedule_stays_in_deadlock_where_random_slopes_recover():
     """Rows and columns only (the row/column SFT's lines, Sec. 2.1) against random slopes on the
     Fig. 1 deadlock instance and at K = 2 N0 on 256 x 256: the GPU matches the oracle either way."""
