@@ -78,7 +78,7 @@ typedef struct {
                         FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a
                         guard band around a threshold -- the verdicts are the same either way */
   int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice (synchronous
-                        through L1 on paths 1 and 2, mode 3 on path 3), 1 = synchronous through L1,
+                        through L1, except mode 3 on path 3 for L_max < 2048), 1 = synchronous through L1,
                         2 = synchronous cached in L2 only, 3 = asynchronous copies (cp.async) of the
                         next iteration's lines into a shared-memory buffer while the current one
                         computes.  On the register-FFT path modes 1 and 2 prefetch the next

@@ -606,10 +606,11 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
 // deduplicates keys is split into D+1 contiguous slices, one per rank, and the entry counter is
 // rank 0's.  An insert claims its slot wherever it lies and writes the entry into every replica.
 // Two cluster barriers per iteration: after the peel (every line's bins final) and after the
-// decode (every replica final).  Per CTA: one line, its FFT partner, the prefetch buffer, the
-// twiddles, 12 bytes per set entry and 8 bytes per index slot / (D+1).
+// decode (every replica final).  Per CTA: one line, its FFT partner and the prefetch buffer (each
+// with room for fft_line's padding), the twiddles and the per-stage twiddles, 12 bytes per set
+// entry and 8 bytes per index slot / (D+1).
 struct CLayout {
-  size_t bufA, bufB, bufC, tw, sort, la, lkey, hkey, hidx, total;
+  size_t bufA, bufB, bufC, tw, stw, sort, la, lkey, hkey, hidx, total;
   int hc;   // index slots per rank
 };
 
@@ -617,14 +618,16 @@ static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap,
   auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
   CLayout s{};
   const size_t line = (size_t)L_max * sizeof(float2);
+  const size_t pline = ((size_t)L_max + (size_t)(L_max - 1) / 16 + 1) * sizeof(float2);   // padq(L - 1) + 1
   size_t P = 1;
   while (P < (size_t)k_cap) P <<= 1;
   s.hc = (hash_cap + D) / (D + 1);
   size_t off = 0;
-  s.bufA = off; off = al(off + line);
-  s.bufB = off; off = al(off + line);
-  s.bufC = off; off = al(off + (prefetch ? line : 0));
+  s.bufA = off; off = al(off + pline);
+  s.bufB = off; off = al(off + pline);
+  s.bufC = off; off = al(off + (prefetch ? pline : 0));
   s.tw = off; off = al(off + line);
+  s.stw = off; off = al(off + line);
   // the output sort (rank 0, after the last barrier) reuses the line buffers: 2 P ints
   s.sort = 0;
   const size_t sort_bytes = al(2 * P * sizeof(int));
@@ -738,10 +741,16 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
   float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  float2* stws = reinterpret_cast<float2*>(smem + lay.stw);
   const float2* la = reinterpret_cast<const float2*>(smem + lay.la);
   const int* lkey = reinterpret_cast<const int*>(smem + lay.lkey);
 
   load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
+  {
+    const int L = A.tab.shapes[si].L;
+    const float2* t = A.tab.twiddles + A.tab.shapes[si].stw_off;
+    for (int i = threadIdx.x; i < L - 1; i += blockDim.x) stws[i] = t[i];
+  }
   if (threadIdx.x <= D) s_base[threadIdx.x] = cluster.map_shared_rank(smem, (int)threadIdx.x);
   {
     int* hk = reinterpret_cast<int*>(smem + lay.hkey);
@@ -817,7 +826,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
       gather_one_line<D, 0, false>(bufA, x, sh, al, ta, rank);
     }
     __syncthreads();
-    float2* bins = fft_lines(cur, bufB, 1, sh, tws, 1.0f / (float)L);
+    float2* bins = fft_line(cur, bufB, sh, tws, stws, 1.0f / (float)L);
     peel_line_keys<D>(bins, sh, la, lkey, n_set, s_ca, s_ct, tws, rank);
     cluster.sync();   // every line peeled
 
@@ -1453,10 +1462,18 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
           const double ang = 2.0 * M_PI * (double)q / (double)L;
           tw_pool.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
         }
+        // per-stage table of the one-line FFT: entry i Ns + k - 1 = exp(-j 2 pi i k tstep / L)
+        std::vector<float2> stw((size_t)std::max(0LL, L - 1));
+        for (int st = 0, nss = 1; st < sh.nst; nss *= sh.radix[st], ++st)
+          for (int i = 1; i < sh.radix[st]; ++i)
+            for (int k = 0; k < nss; ++k)
+              stw[(size_t)i * nss + k - 1] = tw_pool[off + (size_t)i * k * sh.tstep[st]];
+        tw_pool.insert(tw_pool.end(), stw.begin(), stw.end());
         sh.tw_off = off;
       } else {
         sh.tw_off = t->second;
       }
+      sh.stw_off = sh.tw_off + (int)L;
       si = (int)P->shapes.size();
       shape_id[dv] = si;
       P->shapes.push_back(sh);
@@ -1525,9 +1542,11 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   const bool cluster_auto = pr.fft_path == 0 && !P->warp_path && P->L_max >= 1024 && batch <= 2 * sms &&
                             recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false).total + static_reserve <= (size_t)optin;
   if ((pr.fft_path == 3 || cluster_auto) && batch > 0) {
-    // one line, its FFT partner, the twiddles and a replica of the recovered list per CTA; the
-    // next iteration's line is prefetched unless a synchronous gather mode is requested
-    const bool pf_c = pr.gather_mode == 0 || pr.gather_mode == 3;
+    // one line, its FFT partner, the twiddles and a replica of the recovered list per CTA.  The
+    // library's choice (measured on 240 x 256 and 1024^2): lines of 2048 or more with 1024-thread
+    // CTAs and synchronous gathers, shorter lines with 512 threads and the next iteration's line
+    // prefetched
+    const bool pf_c = pr.gather_mode == 3 || (pr.gather_mode == 0 && P->L_max < 2048);
     CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c);
     P->prefetch = pf_c;
     if (cl.total + static_reserve > (size_t)optin) {
@@ -1543,6 +1562,8 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     P->smem = cl.total;
     if (pr.threads > 0) {
       P->threads = pr.threads;
+    } else if (P->L_max >= 2048) {
+      P->threads = 1024;
     } else {
       int t = 128;
       while (2 * t < P->L_max && t < 512) t <<= 1;
@@ -2233,6 +2254,7 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
         sh.fns[s] = make_fastdiv(ns);
         ns *= sh.radix[s];
       }
+      sh.stw_off = -1;  // no per-stage table: the one-CTA-per-signal kernel does not use it
       int reuse = -1;   // twiddle table shared by shapes with the same L
       for (int q = 0; q < n_shapes && reuse < 0; ++q)
         if (shapes[q].L == sh.L) reuse = shapes[q].tw_off;

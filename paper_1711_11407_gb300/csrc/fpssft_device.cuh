@@ -41,7 +41,7 @@ struct Shape {
   int N;                     // number of grid points
   int nst;                   // FFT stages
   int tw_off;                // offset of the L-entry twiddle table in the pool
-  int pad_;
+  int stw_off;               // offset of the (L-1)-entry per-stage twiddle table (-1: none)
   int dims[kMaxD];
   int strides[kMaxD];        // row-major element strides (last dimension fastest)
   int c[kMaxD];              // L / N_d
@@ -359,6 +359,105 @@ __device__ __forceinline__ float2* fft_lines(float2* buf0, float2* buf1, int nli
     in = out;
     out = t;
     Ns *= R;
+  }
+  return in;
+}
+
+// One line per CTA (the cluster path), with two changes that remove most shared-memory bank
+// conflicts of the stages above:
+//  * the intermediate buffers (not the first stage's input, not the last stage's output) keep one
+//    float2 of padding after every 16 elements when the stage writing them has radix 2, 4 or 8 and
+//    span Ns < 16: the writes out[(j - k) R + k + i Ns] of consecutive butterflies are then spread
+//    over distinct banks instead of R/Ns-way conflicts;
+//  * the twiddles w^(i k L/(Ns R)) of each stage come from a per-stage table laid out as
+//    stw[i Ns + k - 1] (i = 1..R-1, k < Ns; the stages tile [0, L-1) exactly since
+//    sum_s (R_s - 1) Ns_s = L - 1), read at consecutive addresses by consecutive butterflies.
+// Buffers need padq(L - 1) + 1 elements.
+__device__ __forceinline__ int padq(int q) { return q + (q >> 4); }
+
+__device__ __forceinline__ bool stage_pads_output(const Shape& sh, int s, int Ns) {
+  const int R = sh.radix[s];
+  return s < sh.nst - 1 && (R == 2 || R == 4 || R == 8) && Ns < 16;
+}
+
+template <int R>
+__device__ __forceinline__ void fft_stage_line(const float2* __restrict__ in, float2* __restrict__ out, int L, int Ns,
+                                               const FastDiv& fns, const float2* __restrict__ stw, bool pin, bool pout,
+                                               float sc) {
+  const int nb = L / R;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int k = fmod_(j, fns);
+    float2 v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int q = j + i * nb;
+      v[i] = in[pin ? padq(q) : q];
+    }
+    if (k != 0) {
+#pragma unroll
+      for (int i = 1; i < R; ++i) v[i] = cmul(v[i], stw[i * Ns + k - 1]);
+    }
+    butterfly<R>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int q = base + i * Ns;
+      out[pout ? padq(q) : q] = cscale(v[i], sc);
+    }
+  }
+}
+
+__device__ __forceinline__ void fft_stage_line_generic(const float2* __restrict__ in, float2* __restrict__ out, int L,
+                                                       int Ns, int R, const FastDiv& fns, const float2* __restrict__ tw,
+                                                       const float2* __restrict__ stw, bool pin, bool pout, float sc) {
+  const int nb = L / R;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int k = fmod_(j, fns);
+    const int base = (j - k) * R + k;
+    for (int q = 0; q < R; ++q) {
+      float2 acc = make_float2(0.f, 0.f);
+      int x = 0;                     // (i q) mod R
+      for (int i = 0; i < R; ++i) {
+        const int qi = j + i * nb;
+        float2 v = in[pin ? padq(qi) : qi];
+        if (k != 0 && i != 0) v = cmul(v, stw[i * Ns + k - 1]);
+        acc = cadd(acc, cmul(v, tw[x * nb]));   // exp(-j 2 pi x / R) = tw[x L / R]
+        x += q;
+        if (x >= R) x -= R;
+      }
+      const int qo = base + q * Ns;
+      out[pout ? padq(qo) : qo] = cscale(acc, sc);
+    }
+  }
+}
+
+// Forward DFT of one line of length sh.L in buf0 (natural order in, natural order out), scaled by
+// `scale`; buf1 is the ping-pong partner.  A barrier ends every stage; returns the result buffer.
+__device__ __forceinline__ float2* fft_line(float2* buf0, float2* buf1, const Shape& sh, const float2* __restrict__ tw,
+                                            const float2* __restrict__ stw, float scale) {
+  float2* in = buf0;
+  float2* out = buf1;
+  int Ns = 1;
+  bool pin = false;
+  const int L = sh.L;
+  for (int s = 0; s < sh.nst; ++s) {
+    const int R = sh.radix[s];
+    const float sc = (s == sh.nst - 1) ? scale : 1.f;
+    const bool pout = stage_pads_output(sh, s, Ns);
+    switch (R) {
+      case 2: fft_stage_line<2>(in, out, L, Ns, sh.fns[s], stw, pin, pout, sc); break;
+      case 3: fft_stage_line<3>(in, out, L, Ns, sh.fns[s], stw, pin, pout, sc); break;
+      case 4: fft_stage_line<4>(in, out, L, Ns, sh.fns[s], stw, pin, pout, sc); break;
+      case 5: fft_stage_line<5>(in, out, L, Ns, sh.fns[s], stw, pin, pout, sc); break;
+      case 8: fft_stage_line<8>(in, out, L, Ns, sh.fns[s], stw, pin, pout, sc); break;
+      default: fft_stage_line_generic(in, out, L, Ns, R, sh.fns[s], tw, stw, pin, pout, sc); break;
+    }
+    __syncthreads();
+    float2* t = in;
+    in = out;
+    out = t;
+    Ns *= R;
+    pin = pout;
   }
   return in;
 }

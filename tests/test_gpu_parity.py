@@ -481,7 +481,8 @@ def test_unfused_steps_reject_sets_larger_than_shared_memory():
         with pytest.raises(_lib.FpssftError) as e:
             call()
         assert e.value.status == _lib.ERR_UNSUPPORTED
-    out = plan.recover(*to_dev(wl))
+    cubes, offs, _, _ = to_dev(wl)
+    out = plan.recover(cubes, offs, al, ta)
     torch.cuda.synchronize()
     assert int(out.status[0]) == 0 and int(out.iters[0]) == 1
 
