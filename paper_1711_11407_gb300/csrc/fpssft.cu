@@ -609,12 +609,22 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
 // decode (every replica final).  Per CTA: one line, its FFT partner and the prefetch buffer (each
 // with room for fft_line's padding), the twiddles and the per-stage twiddles, 12 bytes per set
 // entry and 8 bytes per index slot / (D+1).
+// GS variant, for sets too large for that: one copy of the list, the whole index and the counter
+// live in a per-signal slice of global workspace (cluster_gset_stride bytes), read through L2
+// (ld.global.cg: lines written by other SMs are never served from a stale L1 copy); shared memory
+// holds only the line buffers and twiddles.
 struct CLayout {
   size_t bufA, bufB, bufC, tw, stw, sort, la, lkey, hkey, hidx, total;
   int hc;   // index slots per rank
 };
 
-static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap, int hash_cap, bool prefetch) {
+static __host__ __device__ size_t cluster_gset_stride(int k_cap, int hash_cap) {
+  const size_t b = (size_t)k_cap * (sizeof(float2) + sizeof(int)) + (size_t)hash_cap * 2 * sizeof(int) + sizeof(int);
+  return (b + 255) & ~size_t(255);
+}
+
+static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap, int hash_cap, bool prefetch,
+                                                    bool gset = false) {
   auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
   CLayout s{};
   const size_t line = (size_t)L_max * sizeof(float2);
@@ -628,6 +638,11 @@ static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap,
   s.bufC = off; off = al(off + (prefetch ? pline : 0));
   s.tw = off; off = al(off + line);
   s.stw = off; off = al(off + line);
+  if (gset) {   // the set, and the output sort's buffers, are in global workspace
+    s.sort = s.la = s.lkey = s.hkey = s.hidx = off;
+    s.total = off;
+    return s;
+  }
   // the output sort (rank 0, after the last barrier) reuses the line buffers: 2 P ints
   s.sort = 0;
   const size_t sort_bytes = al(2 * P * sizeof(int));
@@ -694,16 +709,46 @@ __device__ __forceinline__ bool cluster_insert(unsigned char* const* base, const
   return false;   // unreachable at load factor <= 1/2
 }
 
-// Peel of line j from the (key, a) list: entry i lands in bin m with phase p (j = 0) or
-// p + c_{j-1} k_{j-1}.
+// a5 of the GS variant: the same contract with one global copy of the list, index and counter.
 template <int D>
+__device__ __forceinline__ bool cluster_insert_g(float2* g_la, int* g_lkey, int* g_hkey, int* g_hidx, int* g_count,
+                                                 int k_cap, int hash_bits, int key, float2 a) {
+  const unsigned mask = (1u << hash_bits) - 1u;
+  unsigned h = hash_slot(key, hash_bits);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(&g_hkey[h], kEmpty, key);
+    if (old == kEmpty) {
+      const int idx = atomicAdd(g_count, 1);
+      if (idx >= k_cap) {
+        g_hidx[h] = -1;
+        return false;
+      }
+      g_lkey[idx] = key;
+      g_la[idx] = a;
+      g_hidx[h] = idx;
+      return true;
+    }
+    if (old == key) {
+      const int idx = __ldcg(&g_hidx[h]);
+      if (idx < 0 || idx >= k_cap) return false;   // overflowed claim (or a repeated resume key)
+      g_la[idx] = cadd(__ldcg(&g_la[idx]), a);
+      return true;
+    }
+    h = (h + 1u) & mask;
+  }
+  return false;   // unreachable at load factor <= 1/2
+}
+
+// Peel of line j from the (key, a) list: entry i lands in bin m with phase p (j = 0) or
+// p + c_{j-1} k_{j-1}.  L2ONLY: the list is read through L2 (global list of the GS variant).
+template <int D, bool L2ONLY>
 __device__ __forceinline__ void peel_line_keys(float2* bins, const Shape& sh, const float2* la, const int* lkey,
                                                int count, const int* ca, const int* ct,
                                                const float2* __restrict__ tw, int j) {
   const int L = sh.L;
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     int k[D];
-    key_to_k<D>(sh, lkey[i], k);
+    key_to_k<D>(sh, L2ONLY ? __ldcg(lkey + i) : lkey[i], k);
     int msum = 0, psum = 0, shift = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -714,14 +759,14 @@ __device__ __forceinline__ void peel_line_keys(float2* bins, const Shape& sh, co
     const int m = fmod_(msum, sh.fL);
     int q = fmod_(psum, sh.fL) + shift;
     if (q >= L) q -= L;
-    const float2 v = cmulc(la[i], tw[q]);
+    const float2 v = cmulc(L2ONLY ? __ldcg(la + i) : la[i], tw[q]);
     atomicAdd(&bins[m].x, -v.x);
     atomicAdd(&bins[m].y, -v.y);
   }
 }
 
 // One signal per cluster (grid = batch clusters of D+1 CTAs, in the longest-first order).
-template <int D, int MAXT>
+template <int D, int MAXT, bool GS>
 __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -736,14 +781,22 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   const int b = A.tab.order[blockIdx.x / (D + 1)];
   const int si = A.tab.sig_shape[b];
   const bool pf = A.prefetch != 0;
-  const CLayout lay = recover_layout_c(D, A.L_max, A.k_cap, 1 << A.hash_bits, pf);
+  const int hash_cap = 1 << A.hash_bits;
+  const CLayout lay = recover_layout_c(D, A.L_max, A.k_cap, hash_cap, pf, GS);
   float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
   float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
   float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
   float2* stws = reinterpret_cast<float2*>(smem + lay.stw);
-  const float2* la = reinterpret_cast<const float2*>(smem + lay.la);
-  const int* lkey = reinterpret_cast<const int*>(smem + lay.lkey);
+  // GS: this signal's slice of global workspace holds the list, the index and the counter
+  unsigned char* ws = GS ? A.gm_ws + (size_t)(blockIdx.x / (D + 1)) * A.gm_stride : nullptr;
+  float2* g_la = reinterpret_cast<float2*>(ws);
+  int* g_lkey = reinterpret_cast<int*>(ws + (size_t)A.k_cap * sizeof(float2));
+  int* g_hkey = g_lkey + A.k_cap;
+  int* g_hidx = g_hkey + hash_cap;
+  int* g_count = g_hidx + hash_cap;
+  const float2* la = GS ? g_la : reinterpret_cast<const float2*>(smem + lay.la);
+  const int* lkey = GS ? g_lkey : reinterpret_cast<const int*>(smem + lay.lkey);
 
   load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
   {
@@ -752,7 +805,12 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     for (int i = threadIdx.x; i < L - 1; i += blockDim.x) stws[i] = t[i];
   }
   if (threadIdx.x <= D) s_base[threadIdx.x] = cluster.map_shared_rank(smem, (int)threadIdx.x);
-  {
+  if (GS) {   // every rank clears a (D+1)-th of the global index
+    const int hcs = (hash_cap + D) / (D + 1);
+    const int h1 = min(hash_cap, (rank + 1) * hcs);
+    for (int i = rank * hcs + threadIdx.x; i < h1; i += blockDim.x) g_hkey[i] = kEmpty;
+    if (rank == 0 && threadIdx.x == 0) *g_count = 0;
+  } else {
     int* hk = reinterpret_cast<int*>(smem + lay.hkey);
     for (int i = threadIdx.x; i < lay.hc; i += blockDim.x) hk[i] = kEmpty;
   }
@@ -764,7 +822,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   }
   cluster.sync();   // every CTA started and initialised before any remote access
 
-  int* c_count = cluster.map_shared_rank(&s_count, 0);
+  int* c_count = GS ? g_count : cluster.map_shared_rank(&s_count, 0);
   int* c_ovf = cluster.map_shared_rank(&s_ovf, 0);
   int* c_t0 = cluster.map_shared_rank(s_t0, 0);
   const float2* x = A.cubes + A.offsets[b];
@@ -782,13 +840,15 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
           k[d] = ok_out[i * D + d];
           key += k[d] * sh.strides[d];
         }
-        if (on_grid<D>(sh, k) && !cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, oa_out[i]))
-          atomicOr(c_ovf, 1);
+        const bool ok = !on_grid<D>(sh, k) ||
+                        (GS ? cluster_insert_g<D>(g_la, g_lkey, g_hkey, g_hidx, g_count, A.k_cap, A.hash_bits, key, oa_out[i])
+                            : cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, oa_out[i]));
+        if (!ok) atomicOr(c_ovf, 1);
       }
     }
     cluster.sync();
   }
-  int n_set = min(*c_count, A.k_cap);
+  int n_set = min(GS ? __ldcg(g_count) : *c_count, A.k_cap);
   const bool stop = *c_ovf != 0;
 
   const int L = sh.L;
@@ -827,7 +887,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     }
     __syncthreads();
     float2* bins = fft_line(cur, bufB, sh, tws, stws, 1.0f / (float)L);
-    peel_line_keys<D>(bins, sh, la, lkey, n_set, s_ca, s_ct, tws, rank);
+    peel_line_keys<D, GS>(bins, sh, la, lkey, n_set, s_ca, s_ct, tws, rank);
     cluster.sync();   // every line peeled
 
     const size_t boff = reinterpret_cast<unsigned char*>(bins) - smem;
@@ -857,12 +917,14 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
       }
       if (fmod_(msum, sh.fL) != m) continue;                            // T3
       const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tws, A.th.amp_average != 0);
-      if (!cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, a)) my_ovf = true;
+      const bool ok = GS ? cluster_insert_g<D>(g_la, g_lkey, g_hkey, g_hidx, g_count, A.k_cap, A.hash_bits, key, a)
+                         : cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, a);
+      if (!ok) my_ovf = true;
     }
     if (my_t0) atomicAdd(c_t0 + par, my_t0);
     if (my_ovf) atomicOr(c_ovf, 1);
     cluster.sync();   // every insert landed in every replica
-    n_set = min(*c_count, A.k_cap);
+    n_set = min(GS ? __ldcg(g_count) : *c_count, A.k_cap);
     iters = t + 1;
     if ((A.early_stop && c_t0[par] == 0) || *c_ovf != 0) break;   // the same verdict on every rank
   }
@@ -870,23 +932,55 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   cluster.sync();   // no rank reads another's shared memory past this point
 
   if (rank != 0) return;
-  SetView set{};
-  set.la = reinterpret_cast<float2*>(smem + lay.la);
-  set.lkey = reinterpret_cast<int*>(smem + lay.lkey);
-  set.k_cap = A.k_cap;
+  // output order: a bitmap of the grid points in the shared memory the set does not use (all of it
+  // with GS), else sorted (key, position) pairs
+  {
+    auto get = [&](int i, int& key, float2& a) -> bool {
+      a = GS ? __ldcg(la + i) : la[i];
+      if (!keep_amplitude(a, A.th)) return false;
+      key = GS ? __ldcg(lkey + i) : lkey[i];
+      return true;
+    };
+    auto put = [&](int r, int key, float2 a) {
+      int k[D];
+      key_to_k<D>(sh, key, k);
+#pragma unroll
+      for (int d = 0; d < D; ++d) ok_out[r * D + d] = k[d];
+      oa_out[r] = a;
+    };
+    if (emit_by_bitmap(n_set, sh.N, smem, GS ? lay.total : lay.la, &s_n, get, put)) {
+      if (threadIdx.x == 0) {
+        A.out_count[b] = s_n;
+        A.out_iters[b] = iters;
+        A.out_status[b] = s_ovf ? kStatusCapacity : 0;
+      }
+      return;
+    }
+  }
   int P = 1;
   while (P < A.k_cap) P <<= 1;
-  int* skey = reinterpret_cast<int*>(smem + lay.sort);   // the line buffers, free now
-  int* sidx = skey + P;
-  sort_kept(set, n_set, A.th, skey, sidx, &s_n);
+  // sort buffers: the line buffers, free now, or (GS) the global index
+  int* skey = GS ? g_hkey : reinterpret_cast<int*>(smem + lay.sort);
+  int* sidx = GS ? g_hidx : skey + P;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_set; i += blockDim.x) {
+    if (keep_amplitude(GS ? __ldcg(la + i) : la[i], A.th)) {
+      const int pos = atomicAdd(&s_n, 1);
+      skey[pos] = GS ? __ldcg(lkey + i) : lkey[i];
+      sidx[pos] = i;
+    }
+  }
+  __syncthreads();
   const int n = s_n;
+  sort_pairs(skey, sidx, n);
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const int i = sidx[r];
     int k[D];
-    key_to_k<D>(sh, set.lkey[i], k);
+    key_to_k<D>(sh, skey[r], k);
 #pragma unroll
     for (int d = 0; d < D; ++d) ok_out[r * D + d] = k[d];
-    oa_out[r] = set.la[i];
+    oa_out[r] = GS ? __ldcg(la + i) : la[i];
   }
   if (threadIdx.x == 0) {
     A.out_count[b] = n;
@@ -1266,6 +1360,7 @@ struct fpssft_plan_s {
   bool warp_path = false;   // k_recover_w (register FFT per line) instead of k_recover
   bool gm_path = false;     // k_recover with lines and set in global workspace
   bool cluster_path = false;   // k_recover_c (one CTA per line, a cluster of D+1 CTAs per signal)
+  bool cluster_gs = false;     // ... with the recovered set in global workspace (GS variant)
   bool lines_in_smem = true;   // fpssft_project / _lines / _adjoint / _synth usable
   bool set_in_smem = true;     // fpssft_decode / _finalize usable (one signal's set in one CTA)
   unsigned char* d_gm_ws = nullptr;
@@ -1540,24 +1635,39 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   // library choice: long lines and no more signals than twice the SM count go to the cluster
   // path when it fits (one CTA per signal would leave SMs idle and run the lines one by one)
   const bool cluster_auto = pr.fft_path == 0 && !P->warp_path && P->L_max >= 1024 && batch <= 2 * sms &&
-                            recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false).total + static_reserve <= (size_t)optin;
+                            recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false, true).total + static_reserve <= (size_t)optin;
   if ((pr.fft_path == 3 || cluster_auto) && batch > 0) {
     // one line, its FFT partner, the twiddles and a replica of the recovered list per CTA.  The
     // library's choice (measured on 240 x 256 and 1024^2): lines of 2048 or more with 1024-thread
     // CTAs and synchronous gathers, shorter lines with 512 threads and the next iteration's line
     // prefetched
     const bool pf_c = pr.gather_mode == 3 || (pr.gather_mode == 0 && P->L_max < 2048);
+    // the set in shared memory if it fits (with, then without the prefetch buffer), else in
+    // global workspace
+    const size_t cap = (size_t)optin - static_reserve;
+    bool gs = false;
     CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c);
     P->prefetch = pf_c;
-    if (cl.total + static_reserve > (size_t)optin) {
+    if (cl.total > cap && pf_c) {
       cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false);
       P->prefetch = false;
     }
-    if (cl.total + static_reserve > (size_t)optin) {
+    if (cl.total > cap) {
+      gs = true;
+      cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c, true);
+      P->prefetch = pf_c;
+      if (cl.total > cap && pf_c) {
+        cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false, true);
+        P->prefetch = false;
+      }
+    }
+    if (cl.total > cap) {
       delete P;
-      return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 3: one line, its twiddles and the recovered set exceed one CTA's shared memory");
+      return fail(FPSSFT_ERR_UNSUPPORTED, "fft_path 3: one line and its twiddles exceed one CTA's shared memory");
     }
     P->cluster_path = true;
+    P->cluster_gs = gs;
+    if (gs) P->gm_stride = cluster_gset_stride(pr.k_cap, 1 << hb);
     P->tw_smem = true;
     P->smem = cl.total;
     if (pr.threads > 0) {
@@ -1635,7 +1745,8 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     constexpr int DD = decltype(Dc)::value;
     if (P->gm_path) P->threads = std::min(P->threads, 512);
     const void* kfn = P->warp_path ? (P->prefetch ? (const void*)k_recover_w<DD, true> : (const void*)k_recover_w<DD, false>)
-                    : P->cluster_path ? (P->threads > 512 ? (const void*)k_recover_c<DD, 1024> : (const void*)k_recover_c<DD, 512>)
+                    : P->cluster_path ? (P->cluster_gs ? (P->threads > 512 ? (const void*)k_recover_c<DD, 1024, true> : (const void*)k_recover_c<DD, 512, true>)
+                                                        : (P->threads > 512 ? (const void*)k_recover_c<DD, 1024, false> : (const void*)k_recover_c<DD, 512, false>))
                     : P->gm_path ? (const void*)k_recover<DD, 512, true>
                     : (P->threads > 512 ? (const void*)k_recover<DD, 1024> : (const void*)k_recover<DD, 512>);
     cudaError_t e2 = ensure_dynamic_smem(kfn, P->smem);
@@ -1664,6 +1775,10 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
     P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
     if (P->cluster_path) P->grid = batch * (DD + 1);   // one cluster per signal, not persistent
+    if (P->cluster_gs) {   // one slice of global workspace per signal
+      const cudaError_t ea = cudaMalloc(&P->d_gm_ws, (size_t)batch * P->gm_stride);
+      if (ea != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, std::string("workspace for the cluster path's sets: ") + cudaGetErrorString(ea));
+    }
     if (P->gm_path) {   // cap the persistent grid: every CTA owns a workspace slice
       P->grid = std::max(1, std::min(batch, 2 * P->sm_count));
       const size_t bytes = (size_t)P->grid * P->gm_stride;
@@ -1720,7 +1835,7 @@ extern "C" fpssft_status fpssft_plan_get_info(fpssft_plan_t P, fpssft_plan_info*
   info->twiddles_in_smem = P->tw_smem ? 1 : 0;
   info->prefetch = P->prefetch ? 1 : 0;
   info->fft_path = P->cluster_path ? 3 : P->warp_path ? 2 : 1;
-  info->global_workspace = P->gm_path ? 1 : 0;
+  info->global_workspace = (P->gm_path || P->cluster_gs) ? 1 : 0;
   return FPSSFT_OK;
 }
 
@@ -1838,10 +1953,14 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
       cfg.stream = s;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      if (P->threads > 512)
-        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 1024>, A));
+      if (P->cluster_gs && P->threads > 512)
+        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 1024, true>, A));
+      else if (P->cluster_gs)
+        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 512, true>, A));
+      else if (P->threads > 512)
+        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 1024, false>, A));
       else
-        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 512>, A));
+        FPSSFT_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_recover_c<DD, 512, false>, A));
     } else if (P->gm_path) {
       k_recover<DD, 512, true><<<P->grid, P->threads, 0, s>>>(A);
     } else if (P->threads > 512) {

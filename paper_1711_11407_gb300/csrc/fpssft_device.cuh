@@ -827,6 +827,79 @@ __device__ __forceinline__ void sort_pairs(int* skey, int* sidx, int n) {
   }
 }
 
+// Output in order of linear index through a bitmap of the N grid points held in `region`
+// (needs 4 (ceil(N/32) + blockDim) bytes; false: does nothing).  get(i, key, a) says whether entry
+// i < count is kept and gives its key and amplitude; put(r, key, a) writes output row r.  The
+// position of a kept key is the number of set bits below it: bits set by atomicOr, popcounts
+// summed per thread over a contiguous chunk of words, an exclusive scan of the chunk sums by warp
+// 0, popcounts inside the chunk.  *n_out = number of entries written.  All threads must call it.
+template <typename Get, typename Put>
+__device__ __forceinline__ bool emit_by_bitmap(int count, int N, unsigned char* region, size_t region_bytes,
+                                               int* n_out, Get get, Put put) {
+  const int bd = blockDim.x;
+  const int tid = threadIdx.x;
+  const int W = (N + 31) >> 5;
+  if (((size_t)W + (size_t)bd) * sizeof(unsigned) > region_bytes) return false;
+  unsigned* bm = reinterpret_cast<unsigned*>(region);
+  int* part = reinterpret_cast<int*>(region + region_bytes) - bd;   // chunk sums, after the bitmap
+  for (int w = tid; w < W; w += bd) bm[w] = 0u;
+  __syncthreads();
+  for (int i = tid; i < count; i += bd) {
+    int key;
+    float2 a;
+    if (get(i, key, a)) atomicOr(&bm[key >> 5], 1u << (key & 31));
+  }
+  __syncthreads();
+  const int chunk = (W + bd - 1) / bd;
+  {
+    const int w0 = min(W, tid * chunk);
+    const int w1 = min(W, w0 + chunk);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(bm[w]);
+    part[tid] = c;
+  }
+  __syncthreads();
+  if (tid < 32) {   // lane l scans the run [l per, (l + 1) per) of chunk sums
+    const int per = (bd + 31) >> 5;
+    int sum = 0;
+    for (int q = 0; q < per; ++q) {
+      const int j = tid * per + q;
+      if (j < bd) sum += part[j];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    int run = incl - sum;
+    for (int q = 0; q < per; ++q) {
+      const int j = tid * per + q;
+      if (j < bd) {
+        const int v = part[j];
+        part[j] = run;
+        run += v;
+      }
+    }
+    if (tid == 31) *n_out = incl;
+  }
+  __syncthreads();
+  for (int i = tid; i < count; i += bd) {
+    int key;
+    float2 a;
+    if (get(i, key, a)) {
+      const int w = key >> 5;
+      const int owner = w / chunk;
+      int r = part[owner];
+      for (int u = owner * chunk; u < w; ++u) r += __popc(bm[u]);
+      r += __popc(bm[w] & ((1u << (key & 31)) - 1u));
+      put(r, key, a);
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // Compact the entries with |a| > theta0 into (skey, sidx) and sort them by linear index: on return
 // *n_out is the number kept and sidx[r] the list position of the r-th smallest key.
 __device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thresholds& th, int* skey, int* sidx,

@@ -171,10 +171,65 @@ def test_cluster_path_teacher_forced_noisy_1024_images():
             assert np.allclose(a, nxt.a, rtol=1e-3, atol=0)
 
 
-def test_cluster_path_rejects_sets_that_do_not_fit_shared_memory():
-    from paper_1711_11407_gb300 import _lib
+@pytest.mark.parametrize("case", ["sparse_image_512x576", "single_240x256", "D3_24x32x40"])
+def test_cluster_path_with_the_set_in_global_workspace_matches_oracle(case):
+    """Sets too large for shared memory (k_cap 20000): the cluster path keeps the lines in shared
+    memory and the list, index and counter in global workspace; sets equal the oracle's."""
+    from paper_1711_11407_gb300.api import Plan
+    if case == "sparse_image_512x576":
+        wl, T = S.make_workload("sparse_image_512x576", batch=2), None
+    elif case == "single_240x256":
+        wl, T = S.make_workload("single_240x256"), None
+    else:
+        wl, T = small_batch([(24, 32, 40)], 3, K=lambda N: 60, T=10), 10
+    kw = dict(k_cap=20000, fft_path=3)
+    if T is not None:
+        kw["T"] = T
+    p = configs.params_for(wl, **kw)
+    plan = Plan(wl.dims, p)
+    assert plan.info["fft_path"] == 3 and plan.info["global_workspace"] == 1
+    out = plan.recover(*to_dev(wl))
+    torch.cuda.synchronize()
+    for b in range(wl.batch):
+        Tb = int(plan.T[b])
+        ref = O.recover(wl.cube(b), wl.alpha[b, :Tb], wl.tau[b, :Tb], oracle_params(p, Tb))
+        k, a = out.signal(b)
+        assert_same_set(k, a, ref, f"{case} signal {b}")
+        assert int(out.iters[b]) == ref.iters and int(out.status[b]) == ref.status
+
+
+def test_cluster_path_global_set_capacity_overflow():
+    """K = 8411 frequencies with room for 8000 (a set still too large for shared memory): status
+    FPSSFT_ERR_CAPACITY, 8000 entries kept, the oracle's iteration count."""
     from paper_1711_11407_gb300.api import Plan
     wl = S.make_workload("sparse_image_512x576", batch=1)
-    with pytest.raises(_lib.FpssftError) as e:
-        Plan(wl.dims, configs.params_for(wl, k_cap=20000, fft_path=3))
-    assert e.value.status == _lib.ERR_UNSUPPORTED
+    p = configs.params_for(wl, k_cap=8000, fft_path=3)
+    plan = Plan(wl.dims, p)
+    assert plan.info["global_workspace"] == 1
+    out = plan.recover(*to_dev(wl))
+    torch.cuda.synchronize()
+    T = int(plan.T[0])
+    ref = O.recover(wl.cube(0), wl.alpha[0, :T], wl.tau[0, :T], oracle_params(p, T))
+    assert int(out.status[0]) == O.STATUS_CAPACITY == ref.status
+    assert int(out.iters[0]) == ref.iters
+    assert int(out.count[0]) == ref.k.shape[0]
+
+
+def test_cluster_path_global_set_resume_equals_one_run():
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("single_240x256")
+    full = Plan(wl.dims, configs.params_for(wl, fft_path=3, k_cap=20000))
+    assert full.info["global_workspace"] == 1
+    cubes, offs, al, ta = to_dev(wl)
+    ref = full.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    step = Plan(wl.dims, configs.params_for(wl, T=1, fft_path=3, k_cap=20000))
+    out = step.alloc_output()
+    init = torch.zeros(1, dtype=torch.int32, device=dev())
+    for t in range(int(ref.iters[0])):
+        step.recover(cubes, offs, al[:, t:t + 1].contiguous(), ta[:, t:t + 1].contiguous(), out=out, init_count=init)
+        init.copy_(out.count)
+    torch.cuda.synchronize()
+    k1, a1 = ref.signal(0)
+    k2, a2 = out.signal(0)
+    assert np.array_equal(k1, k2) and np.allclose(a1, a2, rtol=AMP_TOL, atol=0)

@@ -448,9 +448,9 @@ def test_long_lines_and_large_sets_use_global_workspace_and_match_oracle():
     from paper_1711_11407_gb300.api import Plan
     for wl, kcap in ((S.make_workload("sparse_image_512x576", batch=2), 20000),
                      (S.make_workload("single_240x256"), 20000)):
-        p = configs.params_for(wl, k_cap=kcap)
+        p = configs.params_for(wl, k_cap=kcap, fft_path=1)
         plan = Plan(wl.dims, p)
-        assert plan.info["global_workspace"] == 1
+        assert plan.info["global_workspace"] == 1 and plan.info["fft_path"] == 1
         out = plan.recover(*to_dev(wl))
         torch.cuda.synchronize()
         for b in range(wl.batch):
@@ -605,8 +605,10 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
     dims, K = _random_case(rng)
     T = int(rng.integers(3, 16))
     wl = small_batch([dims], 3, K=lambda N: K, T=T, seed=2000 + seed)
-    for path, gm in ((1, 1), (1, 3), (2, 1), (3, 1), (3, 3)):
-        p = configs.params_for(wl, T=T, k_cap=2 * K + 8, fft_path=path, gather_mode=gm)
+    # the last entry forces the cluster path's set into global workspace (k_cap beyond shared memory)
+    for path, gm, kcap in ((1, 1, 2 * K + 8), (1, 3, 2 * K + 8), (2, 1, 2 * K + 8), (3, 1, 2 * K + 8),
+                           (3, 3, 2 * K + 8), (3, 1, 16000)):
+        p = configs.params_for(wl, T=T, k_cap=kcap, fft_path=path, gather_mode=gm)
         try:
             plan = Plan(wl.dims, p)
         except _lib.FpssftError as e:
@@ -617,5 +619,5 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
         for b in range(wl.batch):
             ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, T))
             k, a = out.signal(b)
-            assert_same_set(k, a, ref, f"dims {dims} K {K} path {path} gather {gm} signal {b}")
+            assert_same_set(k, a, ref, f"dims {dims} K {K} path {path} gather {gm} k_cap {kcap} signal {b}")
             assert int(out.iters[b]) == ref.iters and int(out.status[b]) == ref.status
