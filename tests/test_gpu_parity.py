@@ -595,7 +595,7 @@ def _random_case(rng):
     return dims, K
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(32))
 def test_random_shapes_match_oracle_on_every_kernel_path(seed):
     """Seeded random D, shapes (prime and mixed-radix line lengths), sparsity and budgets: every
     applicable kernel path recovers exactly the oracle's set."""
@@ -605,6 +605,7 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
     dims, K = _random_case(rng)
     T = int(rng.integers(3, 16))
     wl = small_batch([dims], 3, K=lambda N: K, T=T, seed=2000 + seed)
+    refs = {}
     # the last entry forces the cluster path's set into global workspace (k_cap beyond shared memory)
     for path, gm, kcap in ((1, 1, 2 * K + 8), (1, 3, 2 * K + 8), (2, 1, 2 * K + 8), (3, 1, 2 * K + 8),
                            (3, 3, 2 * K + 8), (3, 1, 16000)):
@@ -617,7 +618,10 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
         out = plan.recover(*to_dev(wl))
         torch.cuda.synchronize()
         for b in range(wl.batch):
-            ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, T))
+            # k_cap > K on every path, so no set overflows and the oracle's result is the same for all
+            if b not in refs:
+                refs[b] = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, T))
+            ref = refs[b]
             k, a = out.signal(b)
             assert_same_set(k, a, ref, f"dims {dims} K {K} path {path} gather {gm} k_cap {kcap} signal {b}")
             assert int(out.iters[b]) == ref.iters and int(out.status[b]) == ref.status
