@@ -88,11 +88,37 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def strip_comments(src):
+    """C/C++ source without comments and with whitespace runs collapsed (string and character
+    literals kept), so that a comment-only edit leaves the kernel's hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_hash():
+    """Hash of the kernel sources' code (comments and whitespace excluded)."""
     h = hashlib.sha256()
     for p in ("paper_1711_11407_gb300/csrc/fpssft.cu", "paper_1711_11407_gb300/csrc/fpssft_device.cuh"):
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -440,7 +466,10 @@ def main():
                        "fft_path": plan.info["fft_path"], "gather_mode": p.gather_mode,
                        "autotune_ms": tuning},
             "roofline": roofline, "gpu_launches": args.steps, "exact_support_success": success,
-            "mean_iterations": float(np.mean(iters)), "clocks": clk.summary()}
+            "mean_iterations": float(np.mean(iters)),
+            # samples read per signal as a fraction of its cube: iterations (D+1) L / N (Sec. 3's measure)
+            "mean_sample_fraction": float(np.mean(it64 * (wl.D + 1) * L / np.prod(wl.dims.astype(np.float64), axis=1))),
+            "clocks": clk.summary()}
 
     if not args.quick:
         # ---- end to end through the host-buffer call ------------------------------------------

@@ -3,11 +3,13 @@
 // Paper: Wang, Patel, Petropulu, "FPS-SFT: A Multi-dimensional Sparse Fourier Transform Based on
 // the Fourier Projection-slice Theorem", arXiv 1711.11407.  The iteration of Sec. 2.2 (sample the
 // D+1 lines, L-point DFT, subtract the recovered set, decode 1-sparse bins, merge) runs inside one
-// persistent launch for a whole batch: every signal is owned by one CTA for all its iterations,
-// with its bins, twiddles and recovered set on chip, so the only global traffic per iteration is
-// the (D+1) L sample gather.  Two kernels: k_recover_w (one warp per line, register FFT, for
-// L in {32, 64, 128, 256}) and k_recover (shared-memory mixed-radix FFT, any L; with a global-
-// workspace variant for lines or sets too large for shared memory).
+// launch for a whole batch, every signal owned by one CTA (or one cluster of CTAs) for all its
+// iterations with its bins, twiddles and recovered set on chip, so the only global traffic per
+// iteration is the (D+1) L sample gather.  Three kernels: k_recover_w (one warp per line, register
+// FFT, for L in {32, 64, 128, 256}), k_recover (one persistent CTA per signal, shared-memory
+// mixed-radix FFT, any L; with a global-workspace variant for lines or sets too large for shared
+// memory) and k_recover_c (one CTA per line, the D+1 CTAs of a signal forming a thread-block cluster
+// that exchanges bins through distributed shared memory; long lines in small batches).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 

@@ -3,10 +3,10 @@
 // Paper: Wang, Patel, Petropulu, "FPS-SFT: A Multi-dimensional Sparse Fourier Transform Based on
 // the Fourier Projection-slice Theorem", arXiv 1711.11407.
 //
-// Everything here works on one signal per CTA: the D+1 lines of one iteration live in shared
-// memory as [D+1][L] complex64 (line-major), the recovered set lives in shared memory as a dense
-// list plus an open-addressing index, and every phase ends with a CTA barrier issued by the
-// caller.  Integer work (grid points, bins, twiddle indices) is exact; bins are FP32; the
+// The building blocks work on the lines and set one CTA holds: the D+1 lines of one iteration in
+// shared memory as [D+1][L] complex64 (line-major), or one line (fft_line, the cluster path), the
+// recovered set as a dense list plus an open-addressing index (or per-bin buckets, the register
+// path), and every phase ends with a CTA barrier issued by the caller.  Integer work (grid points, bins, twiddle indices) is exact; bins are FP32; the
 // 1-sparsity tests and the phase decode are evaluated in FP64 from the FP32 bins.
 #pragma once
 

@@ -41,13 +41,18 @@ class PlainRecoverer:
         status = torch.zeros(1, dtype=torch.int32, device=dev)
         off = torch.zeros(1, dtype=torch.int64, device=dev)
         iters = 0
+        nvtx = torch.cuda.nvtx   # one range per step of the iteration (visible to ncu --nvtx)
         for t in range(T):
             al = alpha[t:t + 1].reshape(1, 1, D)
             ta = tau[t:t + 1].reshape(1, 1, D)
-            lines = plan.lines(cube, off, al, ta)
-            bins = (torch.fft.fft(lines[..., :L], dim=-1) / L).contiguous()
-            plan.synth(al, ta, k, a, count, accumulate=-1, bins=bins)
-            plan.decode(bins, al, ta, k, a, count, t0, status)
+            with nvtx.range("gather"):
+                lines = plan.lines(cube, off, al, ta)
+            with nvtx.range("line_dft"):
+                bins = (torch.fft.fft(lines[..., :L], dim=-1) / L).contiguous()
+            with nvtx.range("peel"):
+                plan.synth(al, ta, k, a, count, accumulate=-1, bins=bins)
+            with nvtx.range("decode_merge"):
+                plan.decode(bins, al, ta, k, a, count, t0, status)
             iters = t + 1
             if (self.params.early_stop and int(t0.item()) == 0) or int(status.item()) != 0:
                 break
