@@ -114,11 +114,14 @@ def strip_comments(src):
 
 
 def source_hash():
-    """Hash of the kernel sources' code (comments and whitespace excluded)."""
+    """Hash of the kernel sources' code (every file under csrc/, comments and whitespace excluded)."""
     h = hashlib.sha256()
-    for p in ("paper_1711_11407_gb300/csrc/fpssft.cu", "paper_1711_11407_gb300/csrc/fpssft_device.cuh"):
-        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
-            h.update(strip_comments(f.read()).encode())
+    csrc = os.path.join(ROOT, "paper_1711_11407_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                h.update(name.encode())
+                h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 

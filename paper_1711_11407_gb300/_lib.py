@@ -16,7 +16,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libfpssft.so")
 SOURCES = [os.path.join(_HERE, "csrc", "fpssft.cu")]
-DEPENDS = SOURCES + [os.path.join(_HERE, "csrc", "fpssft_device.cuh"), os.path.join(_ROOT, "include", "fpssft.h")]
+DEPENDS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("fpssft_device.cuh", "recover_common.cuh",
+                                                                "recover_shared.cuh", "recover_warp.cuh",
+                                                                "recover_cluster.cuh", "aux_kernels.cuh")] + \
+    [os.path.join(_ROOT, "include", "fpssft.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--expt-relaxed-constexpr", "-shared", "-Xcompiler", "-fPIC"]
 

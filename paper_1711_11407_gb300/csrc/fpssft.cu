@@ -10,7 +10,7 @@
 // mixed-radix FFT, any L; with a global-workspace variant for lines or sets too large for shared
 // memory) and k_recover_c (one CTA per line, the D+1 CTAs of a signal forming a thread-block cluster
 // that exchanges bins through distributed shared memory; long lines in small batches).
-#include <cooperative_groups.h>
+
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,8 +47,6 @@ fpssft_status fail(fpssft_status st, const std::string& msg) {
     }                                                                                            \
   } while (0)
 
-constexpr int kStatusCapacity = FPSSFT_ERR_CAPACITY;
-
 // The dynamic shared-memory limit is a property of the kernel (per device), shared by every plan:
 // raise it when a plan needs more, never lower it under a plan that needs more.
 // (fixed-size table: recording a limit allocates nothing)
@@ -81,1265 +79,17 @@ cudaError_t ensure_dynamic_smem(const void* func, size_t bytes) {
   return r;
 }
 
-struct DeviceTables {
-  const Shape* shapes;
-  const int* sig_shape;
-  const int* sig_T;
-  const int* order;
-  const float2* twiddles;
-};
-
 }  // namespace
 
 // ================================================================================================
 // Kernels
 // ================================================================================================
 
-struct RecoverArgs {
-  const float2* cubes;
-  const int64_t* offsets;
-  const int* alpha;
-  const int* tau;
-  int sched_stride;          // T_max * D
-  DeviceTables tab;
-  int* work_counter;
-  int batch;
-  int k_cap;
-  int hash_bits;
-  int L_max;
-  int tw_smem;
-  int prefetch;
-  int gather_mode;
-  int early_stop;
-  unsigned char* gm_ws;      // lines and recovered set in global memory (lines longer than shared memory)
-  size_t gm_stride;          // bytes of workspace per CTA
-  Thresholds th;
-  const int* init_count;
-  int* out_k;
-  float2* out_a;
-  int* out_count;
-  int* out_iters;
-  int* out_status;
-};
-
-struct SmemLayout {
-  size_t bufA, bufB, bufC, tw, la, lk, lkey, hkey, hidx, total;
-};
-
-// bufA / bufC: the samples of iterations t and t+1 (bufC only when the gather is prefetched);
-// bufB: the FFT's ping-pong partner.
-static __host__ __device__ SmemLayout recover_layout(int D, int L_max, int k_cap, int hash_cap, bool tw_smem,
-                                                     bool prefetch) {
-  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
-  SmemLayout s{};
-  size_t off = 0;
-  const size_t lines = (size_t)(D + 1) * L_max * sizeof(float2);
-  s.bufA = off; off = al(off + lines);
-  s.bufB = off; off = al(off + lines);
-  s.bufC = off; off = al(off + (prefetch ? lines : 0));
-  s.tw = off; off = al(off + (tw_smem ? (size_t)L_max * sizeof(float2) : 0));
-  s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
-  s.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
-  s.lkey = off; off = al(off + (size_t)k_cap * sizeof(int));
-  s.hkey = off; off = al(off + (size_t)hash_cap * sizeof(int));
-  s.hidx = off; off = al(off + (size_t)hash_cap * sizeof(int));
-  s.total = off;
-  return s;
-}
-
-// Copy a Shape into shared memory (cooperatively) and, when twiddles live in shared memory, its
-// twiddle table.  Caller synchronises afterwards.
-__device__ __forceinline__ void load_shape(Shape& sh, const Shape* __restrict__ shapes, int si, float2* tws,
-                                           const float2* __restrict__ twiddles, bool tw_smem) {
-  const int* src = reinterpret_cast<const int*>(shapes + si);
-  int* dst = reinterpret_cast<int*>(&sh);
-  for (int i = threadIdx.x; i < (int)(sizeof(Shape) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-  if (tw_smem) {
-    const int L = shapes[si].L;
-    const float2* t = twiddles + shapes[si].tw_off;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = t[i];
-  }
-}
-
-// GM = true: the same kernel with the lines, the FFT partner and the recovered set in a per-CTA
-// slice of global workspace (L2-resident) instead of shared memory, for lines or sets too large
-// for one CTA's shared memory.  All device functions take generic pointers.
-template <int D, int MAXT, bool GM = false>
-__global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
-  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
-
-  unsigned char* base = GM ? A.gm_ws + (size_t)blockIdx.x * A.gm_stride : smem;
-  const SmemLayout lay = recover_layout(D, A.L_max, A.k_cap, 1 << A.hash_bits, A.tw_smem != 0, A.prefetch != 0);
-  float2* bufA = reinterpret_cast<float2*>(base + lay.bufA);
-  float2* bufB = reinterpret_cast<float2*>(base + lay.bufB);
-  float2* bufC = reinterpret_cast<float2*>(base + lay.bufC);
-  const bool pf = A.prefetch != 0;
-  float2* tws = reinterpret_cast<float2*>(base + lay.tw);
-  SetView set;
-  set.la = reinterpret_cast<float2*>(base + lay.la);
-  set.lk = reinterpret_cast<int*>(base + lay.lk);
-  set.lkey = reinterpret_cast<int*>(base + lay.lkey);
-  set.hkey = reinterpret_cast<int*>(base + lay.hkey);
-  set.hidx = reinterpret_cast<int*>(base + lay.hidx);
-  set.count = &s_count;
-  set.k_cap = A.k_cap;
-  set.hash_bits = A.hash_bits;
-  const int hash_cap = 1 << A.hash_bits;
-
-  int loaded = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
-    __syncthreads();
-    const int qi = s_sig;
-    if (qi >= A.batch) break;
-    const int b = A.tab.order[qi];
-    const int si = A.tab.sig_shape[b];
-    if (si != loaded) {
-      load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, A.tw_smem != 0);
-      loaded = si;
-    }
-    for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) set.hkey[i] = kEmpty;
-    if (threadIdx.x == 0) {
-      s_count = 0;
-      s_ovf = 0;
-    }
-    __syncthreads();
-    const float2* tw = A.tw_smem ? tws : A.tab.twiddles + sh.tw_off;
-    const int L = sh.L;
-    const float2* x = A.cubes + A.offsets[b];
-    int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
-    float2* oa_out = A.out_a + (size_t)b * A.k_cap;
-
-    if (A.init_count != nullptr) {   // resume from a given set
-      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
-      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-        int k[D];
-        int key = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          k[d] = ok_out[i * D + d];
-          key += k[d] * sh.strides[d];
-        }
-        if (on_grid<D>(sh, k) && !set_insert<D>(set, k, key, oa_out[i])) atomicOr(&s_ovf, 1);
-      }
-      __syncthreads();
-    }
-
-    const int T = A.tab.sig_T[b];
-    const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
-    const int* sched_t = A.tau + (size_t)b * A.sched_stride;
-    if (pf && T > 0) gather_lines_async<D>(bufA, x, sh, sched_a, sched_t);
-    int iters = 0;
-    for (int t = 0; t < T; ++t) {
-      const int* al = sched_a + t * D;
-      const int* ta = sched_t + t * D;
-      if (threadIdx.x < D) {
-        const int d = threadIdx.x;
-        s_ca[d] = cmodL(sh, d, al[d]);
-        s_ct[d] = cmodL(sh, d, ta[d]);
-      }
-      float2* cur = (pf && (t & 1)) ? bufC : bufA;
-      if (pf) {
-        // samples of t were requested one iteration ago; request t+1's now, wait for t's
-        if (t + 1 < T) {
-          gather_lines_async<D>((t & 1) ? bufA : bufC, x, sh, al + D, ta + D);
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
-        }
-      } else if (A.gather_mode == 2) {
-        gather_lines<D, 1>(bufA, x, sh, al, ta);
-      } else {
-        gather_lines<D, 0>(bufA, x, sh, al, ta);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) s_t0 = 0;
-      float2* bins = fft_lines(cur, bufB, D + 1, sh, tw, 1.0f / (float)L);
-      peel_set<D>(bins, sh, set, min(s_count, A.k_cap), s_ca, s_ct, tw);
-      __syncthreads();
-      decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf);
-      __syncthreads();
-      iters = t + 1;
-      const bool stop = (A.early_stop && s_t0 == 0) || s_ovf != 0;
-      if (stop) break;
-    }
-
-    if (pf) cp_async_wait<0>();   // a prefetch past the last iteration still lands before reuse
-    // output: keep |a| > theta0, sorted by linear index (hash arrays reused as sort buffers)
-    const int count = min(s_count, A.k_cap);
-    sort_kept(set, count, A.th, set.hkey, set.hidx, &s_n);
-    const int n = s_n;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const int i = set.hidx[r];
-#pragma unroll
-      for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
-      oa_out[r] = set.la[i];
-    }
-    if (threadIdx.x == 0) {
-      A.out_count[b] = n;
-      A.out_iters[b] = iters;
-      A.out_status[b] = s_ovf ? kStatusCapacity : 0;
-    }
-    __syncthreads();
-  }
-}
-
-// ---- warp-per-line variant for L = 32 R (R = 1, 2, 4, 8) ----------------------------------------
-// One CTA of D+1 warps per signal; warp j gathers line j straight into registers and transforms it
-// with warp_fft (no shared-memory staging, no CTA barrier inside the FFT).  Shared memory holds
-// only the bins (bank-swizzled), the twiddles and the bucket set, so several times more signals
-// are resident per SM than with the shared-memory Stockham path.
-struct WLayout {
-  size_t bins, tw, head, la, lk, nxt, stg, total;
-};
-
-static __host__ __device__ WLayout recover_layout_w(int D, int L_max, int k_cap, bool staged = false) {
-  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
-  size_t P = 1;
-  while (P < (size_t)k_cap) P <<= 1;
-  const size_t lines = (size_t)(D + 1) * L_max * sizeof(float2);
-  const size_t sortb = 2 * P * sizeof(int);
-  WLayout w{};
-  size_t off = 0;
-  w.bins = off; off = al(off + (lines > sortb ? lines : sortb));
-  w.tw = off; off = al(off + (size_t)L_max * sizeof(float2));
-  w.head = off; off = al(off + (size_t)L_max * sizeof(int));
-  w.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
-  w.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
-  w.nxt = off; off = al(off + (size_t)k_cap * sizeof(int));
-  w.stg = off; off = al(off + (staged ? lines : 0));
-  w.total = off;
-  return w;
-}
-
-template <int D, int R>
-__device__ __forceinline__ void fft_store_w(float2 (&v)[R], float2* bins, const Shape& sh, const float2* tw, int j,
-                                            int lane, float invL) {
-  warp_fft<R>(v, tw, sh.L, lane);
-  const int br = brev5(lane);
-  float2* out = bins + j * sh.L;
-#pragma unroll
-  for (int k2 = 0; k2 < R; ++k2) out[swz(k2 + R * br)] = cscale(v[k2], invL);
-}
-
-// Sanitised slope and offset of schedule row t (every entry reduced into [0, N_d)).
-template <int D>
-__device__ __forceinline__ void sched_row(const Shape& sh, const int* al, const int* ta, int* alr, int* tar) {
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    alr[d] = fmod_(__ldg(al + d) & 0x3fffffff, sh.fdims[d]);
-    tar[d] = fmod_(__ldg(ta + d) & 0x3fffffff, sh.fdims[d]);
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void peel_set_w(float2* bins, const Shape& sh, const BucketSet& s, int count, const int* ca,
-                                           const int* ct, const float2* __restrict__ tw) {
-  const int L = sh.L;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    int k[D];
-    int msum = 0, psum = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      k[d] = s.lk[d * s.k_cap + i];
-      msum += ca[d] * k[d];
-      psum += ct[d] * k[d];
-    }
-    const int m = fmod_(msum, sh.fL);
-    const int p = fmod_(psum, sh.fL);
-    s.nxt[i] = atomicExch(&s.head[m], i);
-    const float2 a = s.la[i];
-    const int pm = swz(m);
-    float2 v = cmulc(a, tw[p]);
-    atomicAdd(&bins[pm].x, -v.x);
-    atomicAdd(&bins[pm].y, -v.y);
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      int q = p + sh.c[d] * k[d];
-      if (q >= L) q -= L;
-      v = cmulc(a, tw[q]);
-      atomicAdd(&bins[(d + 1) * L + pm].x, -v.x);
-      atomicAdd(&bins[(d + 1) * L + pm].y, -v.y);
-    }
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& sh, const BucketSet& s, const int* ca,
-                                              const int* ct, const float2* __restrict__ tw, const Thresholds& th,
-                                              int* t0, int* ovf, int* accepted) {
-  const int L = sh.L;
-  int my_t0 = 0, my_acc = 0;
-  bool my_ovf = false;
-  for (int m = threadIdx.x; m < L; m += blockDim.x) {
-    const int pm = swz(m);
-    const float2 s0 = bins[pm];
-    float2 sd[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) sd[d] = bins[(d + 1) * L + pm];
-    int k[D];
-    bool counted = false;
-    int v = th.fp64_all ? kUndecided : classify_fp32<D>(s0, sd, sh, th, k, &counted);
-    if (v == kUndecided) {
-      bool c64 = false;
-      v = classify_fp64<D>(s0, sd, sh, th, k, &c64);
-      counted = c64;
-    }
-    my_t0 += counted ? 1 : 0;
-    if (v != kAccept) continue;
-    int msum = 0, psum = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      msum += ca[d] * k[d];
-      psum += ct[d] * k[d];
-    }
-    if (fmod_(msum, sh.fL) != m) continue;                            // T3
-    const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tw, th.amp_average != 0);
-    ++my_acc;
-    if (!bucket_insert<D>(s, m, k, a)) my_ovf = true;
-  }
-  if (my_t0) atomicAdd(t0, my_t0);
-  if (my_acc) atomicAdd(accepted, my_acc);
-  if (my_ovf) atomicOr(ovf, 1);
-}
-
-template <int D>
-__device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh, int count, const Thresholds& th,
-                                            int* skey, int* sidx, int* n_out) {
-  if (threadIdx.x == 0) *n_out = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    if (keep_amplitude(s.la[i], th)) {
-      int key = 0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) key += s.lk[d * s.k_cap + i] * sh.strides[d];
-      const int pos = atomicAdd(n_out, 1);
-      skey[pos] = key;
-      sidx[pos] = i;
-    }
-  }
-  __syncthreads();
-  sort_pairs(skey, sidx, *n_out);
-}
-
-// When every bin that passed T0 in iteration t-1 was decoded and merged, the set is most likely
-// complete and iteration t will find nothing (the early stop): iteration t then does not prefetch
-// t+1.  If the guess is wrong, iteration t+1 gathers its samples synchronously; the results do not
-// depend on the guess.
-template <int D, int R, bool STAGED>
-__device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
-                                         const float2* tws, float2* stg, const float2* __restrict__ x,
-                                         const int* sched_a, const int* sched_t, int T, int warp, int lane,
-                                         float invL, int* s_ca, int* s_ct, int* s_t0, int* s_ovf, int* s_acc) {
-  const int L = sh.L;
-  float2 nxt[STAGED ? 1 : R];
-  float2* my_stg = stg + warp * L;
-  bool have_next = false;      // samples of the current iteration already requested
-  bool likely_done = false;    // every T0 bin of the previous iteration was accepted
-  if (T > 0) {
-    int alr[D], tar[D];
-    sched_row<D>(sh, sched_a, sched_t, alr, tar);
-    if (STAGED)
-      gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
-    else
-      gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
-    have_next = true;
-  }
-  int iters = 0;
-  for (int t = 0; t < T; ++t) {
-    const int* al = sched_a + t * D;
-    const int* ta = sched_t + t * D;
-    if (threadIdx.x < D) {
-      const int d = threadIdx.x;
-      s_ca[d] = cmodL(sh, d, al[d]);
-      s_ct[d] = cmodL(sh, d, ta[d]);
-    }
-    for (int m = threadIdx.x; m < L; m += blockDim.x) set.head[m] = -1;
-    float2 v[R];
-    if (!have_next) {
-      int alr[D], tar[D];
-      sched_row<D>(sh, al, ta, alr, tar);
-      gather_line_regs<D, R>(v, x, sh, alr, tar, warp, lane);
-    } else if (STAGED) {
-      cp_async_wait<0>();
-#pragma unroll
-      for (int i = 0; i < R; ++i) v[i] = my_stg[lane + 32 * i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < R; ++i) v[i] = nxt[STAGED ? 0 : i];
-    }
-    fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
-    have_next = t + 1 < T && !likely_done;
-    if (have_next) {
-      int alr[D], tar[D];
-      sched_row<D>(sh, al + D, ta + D, alr, tar);
-      if (STAGED)
-        gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
-      else
-        gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      *s_t0 = 0;
-      *s_acc = 0;
-    }
-    peel_set_w<D>(bins, sh, set, min(*set.count, A.k_cap), s_ca, s_ct, tws);
-    __syncthreads();
-    decode_bins_w<D>(bins, sh, set, s_ca, s_ct, tws, A.th, s_t0, s_ovf, s_acc);
-    __syncthreads();
-    iters = t + 1;
-    const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
-    if (stop) break;
-    likely_done = A.early_stop && *s_acc == *s_t0;
-  }
-  if (STAGED) cp_async_wait<0>();   // a copy issued past the last iteration lands before reuse
-  return iters;
-}
-
-#ifndef FPSSFT_W_THREADS_PER_SM
-#define FPSSFT_W_THREADS_PER_SM 640   // resident threads per SM the warp path's register budget targets
-#endif
-
-#ifndef FPSSFT_WS_THREADS_PER_SM
-#define FPSSFT_WS_THREADS_PER_SM 768   // same for the variant that stages the prefetch in shared memory
-#endif
-
-template <int D, bool STAGED>
-__global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_SM : FPSSFT_W_THREADS_PER_SM) / (32 * (D + 1)))
-    k_recover_w(RecoverArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n, s_acc;
-  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
-  const WLayout lay = recover_layout_w(D, A.L_max, A.k_cap, STAGED);
-  float2* bins = reinterpret_cast<float2*>(smem + lay.bins);
-  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
-  float2* stg = reinterpret_cast<float2*>(smem + lay.stg);
-  BucketSet set;
-  set.lk = reinterpret_cast<int*>(smem + lay.lk);
-  set.la = reinterpret_cast<float2*>(smem + lay.la);
-  set.head = reinterpret_cast<int*>(smem + lay.head);
-  set.nxt = reinterpret_cast<int*>(smem + lay.nxt);
-  set.count = &s_count;
-  set.k_cap = A.k_cap;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-
-  int loaded = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
-    __syncthreads();
-    const int qi = s_sig;
-    if (qi >= A.batch) break;
-    const int b = A.tab.order[qi];
-    const int si = A.tab.sig_shape[b];
-    if (si != loaded) {
-      load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
-      loaded = si;
-    }
-    if (threadIdx.x == 0) {
-      s_count = 0;
-      s_ovf = 0;
-    }
-    __syncthreads();
-    const int L = sh.L;
-    const int R = L >> 5;
-    const float invL = 1.0f / (float)L;
-    const float2* x = A.cubes + A.offsets[b];
-    int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
-    float2* oa_out = A.out_a + (size_t)b * A.k_cap;
-
-    if (A.init_count != nullptr) {   // resume: the caller's set is appended as given
-      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
-      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-        int k[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) k[d] = ok_out[i * D + d];
-        if (!on_grid<D>(sh, k)) continue;
-        const int idx = atomicAdd(&s_count, 1);
-#pragma unroll
-        for (int d = 0; d < D; ++d) set.lk[d * A.k_cap + idx] = k[d];
-        set.la[idx] = oa_out[i];
-      }
-      __syncthreads();
-    }
-
-    const int T = A.tab.sig_T[b];
-    const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
-    const int* sched_t = A.tau + (size_t)b * A.sched_stride;
-    int iters = 0;
-    switch (R) {
-      case 1: iters = iterate_w<D, 1, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-      case 2: iters = iterate_w<D, 2, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-      case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-      default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-    }
-
-    const int count = min(s_count, A.k_cap);
-    int* skey = reinterpret_cast<int*>(bins);
-    int* sidx = skey + (lay.tw - lay.bins) / (2 * sizeof(int));
-    sort_kept_w<D>(set, sh, count, A.th, skey, sidx, &s_n);
-    const int n = s_n;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const int i = sidx[r];
-#pragma unroll
-      for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
-      oa_out[r] = set.la[i];
-    }
-    if (threadIdx.x == 0) {
-      A.out_count[b] = n;
-      A.out_iters[b] = iters;
-      A.out_status[b] = s_ovf ? kStatusCapacity : 0;
-    }
-    __syncthreads();
-  }
-}
-
-// ---- cluster path: one CTA per line, the D+1 CTAs of a signal form a thread-block cluster -------
-// For long lines one CTA per signal runs the D+1 transforms one after another on one SM and leaves
-// most SMs idle when the batch is small.  Here CTA j of the signal's cluster gathers, transforms
-// and peels line j alone in its own shared memory.  Deciding bin m needs bin m of every line, so
-// each CTA decodes a (D+1)-th of the bins and reads the other lines' bins through distributed
-// shared memory.  The recovered list (key, a) is replicated in every CTA, so each peel reads only
-// local memory (k is recovered from the row-major key); the open-addressing index that
-// deduplicates keys is split into D+1 contiguous slices, one per rank, and the entry counter is
-// rank 0's.  An insert claims its slot wherever it lies and writes the entry into every replica.
-// Two cluster barriers per iteration: after the peel (every line's bins final) and after the
-// decode (every replica final).  Per CTA: one line, its FFT partner and the prefetch buffer (each
-// with room for fft_line's padding), the twiddles and the per-stage twiddles, 12 bytes per set
-// entry and 8 bytes per index slot / (D+1).
-// GS variant, for sets too large for that: one copy of the list, the whole index and the counter
-// live in a per-signal slice of global workspace (cluster_gset_stride bytes), read through L2
-// (ld.global.cg: lines written by other SMs are never served from a stale L1 copy); shared memory
-// holds only the line buffers and twiddles.
-struct CLayout {
-  size_t bufA, bufB, bufC, tw, stw, sort, la, lkey, hkey, hidx, total;
-  int hc;   // index slots per rank
-};
-
-static __host__ __device__ size_t cluster_gset_stride(int k_cap, int hash_cap) {
-  const size_t b = (size_t)k_cap * (sizeof(float2) + sizeof(int)) + (size_t)hash_cap * 2 * sizeof(int) + sizeof(int);
-  return (b + 255) & ~size_t(255);
-}
-
-static __host__ __device__ CLayout recover_layout_c(int D, int L_max, int k_cap, int hash_cap, bool prefetch,
-                                                    bool gset = false) {
-  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
-  CLayout s{};
-  const size_t line = (size_t)L_max * sizeof(float2);
-  const size_t pline = ((size_t)L_max + (size_t)(L_max - 1) / 16 + 1) * sizeof(float2);   // padq(L - 1) + 1
-  size_t P = 1;
-  while (P < (size_t)k_cap) P <<= 1;
-  s.hc = (hash_cap + D) / (D + 1);
-  size_t off = 0;
-  s.bufA = off; off = al(off + pline);
-  s.bufB = off; off = al(off + pline);
-  s.bufC = off; off = al(off + (prefetch ? pline : 0));
-  s.tw = off; off = al(off + line);
-  s.stw = off; off = al(off + line);
-  if (gset) {   // the set, and the output sort's buffers, are in global workspace
-    s.sort = s.la = s.lkey = s.hkey = s.hidx = off;
-    s.total = off;
-    return s;
-  }
-  // the output sort (rank 0, after the last barrier) reuses the line buffers: 2 P ints
-  s.sort = 0;
-  const size_t sort_bytes = al(2 * P * sizeof(int));
-  if (off < sort_bytes) off = sort_bytes;
-  s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
-  s.lkey = off; off = al(off + (size_t)k_cap * sizeof(int));
-  s.hkey = off; off = al(off + (size_t)s.hc * sizeof(int));
-  s.hidx = off; off = al(off + (size_t)s.hc * sizeof(int));
-  s.total = off;
-  return s;
-}
-
-// Frequency components of a row-major linear index (key < N).
-template <int D>
-__device__ __forceinline__ void key_to_k(const Shape& sh, int key, int* k) {
-#pragma unroll
-  for (int d = D - 1; d >= 0; --d) {
-    const int q = fdiv(key, sh.fdims[d]);
-    k[d] = key - q * sh.dims[d];
-    key = q;
-  }
-}
-
-// a5 from any CTA of the cluster: index slot h lives in rank h / hc at h mod hc, the counter is
-// rank 0's, base[r] is rank r's shared memory.  Same contract as set_insert: within one iteration
-// concurrent calls carry distinct keys, and an existing key was written in an earlier iteration
-// (made visible by the cluster barriers).  Returns false on overflow.
-template <int D>
-__device__ __forceinline__ bool cluster_insert(unsigned char* const* base, const CLayout& lay, int* count, int k_cap,
-                                               int hash_bits, int rank, int key, float2 a) {
-  const unsigned mask = (1u << hash_bits) - 1u;
-  unsigned h = hash_slot(key, hash_bits);
-  for (unsigned probe = 0; probe <= mask; ++probe) {
-    const int r = (int)(h / (unsigned)lay.hc);
-    const int i = (int)(h - (unsigned)r * (unsigned)lay.hc);
-    int* hkey = reinterpret_cast<int*>(base[r] + lay.hkey);
-    int* hidx = reinterpret_cast<int*>(base[r] + lay.hidx);
-    const int old = atomicCAS(&hkey[i], kEmpty, key);
-    if (old == kEmpty) {
-      const int idx = atomicAdd(count, 1);
-      if (idx >= k_cap) {
-        hidx[i] = -1;
-        return false;
-      }
-#pragma unroll
-      for (int q = 0; q <= D; ++q) {
-        reinterpret_cast<int*>(base[q] + lay.lkey)[idx] = key;
-        reinterpret_cast<float2*>(base[q] + lay.la)[idx] = a;
-      }
-      hidx[i] = idx;
-      return true;
-    }
-    if (old == key) {
-      const int idx = hidx[i];
-      if (idx < 0 || idx >= k_cap) return false;   // overflowed claim (or a repeated resume key)
-      // every replica holds the same value: add once, write everywhere
-      const float2 s = cadd(reinterpret_cast<const float2*>(base[rank] + lay.la)[idx], a);
-#pragma unroll
-      for (int q = 0; q <= D; ++q) reinterpret_cast<float2*>(base[q] + lay.la)[idx] = s;
-      return true;
-    }
-    h = (h + 1u) & mask;
-  }
-  return false;   // unreachable at load factor <= 1/2
-}
-
-// a5 of the GS variant: the same contract with one global copy of the list, index and counter.
-template <int D>
-__device__ __forceinline__ bool cluster_insert_g(float2* g_la, int* g_lkey, int* g_hkey, int* g_hidx, int* g_count,
-                                                 int k_cap, int hash_bits, int key, float2 a) {
-  const unsigned mask = (1u << hash_bits) - 1u;
-  unsigned h = hash_slot(key, hash_bits);
-  for (unsigned probe = 0; probe <= mask; ++probe) {
-    const int old = atomicCAS(&g_hkey[h], kEmpty, key);
-    if (old == kEmpty) {
-      const int idx = atomicAdd(g_count, 1);
-      if (idx >= k_cap) {
-        g_hidx[h] = -1;
-        return false;
-      }
-      g_lkey[idx] = key;
-      g_la[idx] = a;
-      g_hidx[h] = idx;
-      return true;
-    }
-    if (old == key) {
-      const int idx = __ldcg(&g_hidx[h]);
-      if (idx < 0 || idx >= k_cap) return false;   // overflowed claim (or a repeated resume key)
-      g_la[idx] = cadd(__ldcg(&g_la[idx]), a);
-      return true;
-    }
-    h = (h + 1u) & mask;
-  }
-  return false;   // unreachable at load factor <= 1/2
-}
-
-// Peel of line j from the (key, a) list: entry i lands in bin m with phase p (j = 0) or
-// p + c_{j-1} k_{j-1}.  L2ONLY: the list is read through L2 (global list of the GS variant).
-template <int D, bool L2ONLY>
-__device__ __forceinline__ void peel_line_keys(float2* bins, const Shape& sh, const float2* la, const int* lkey,
-                                               int count, const int* ca, const int* ct,
-                                               const float2* __restrict__ tw, int j) {
-  const int L = sh.L;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    int k[D];
-    key_to_k<D>(sh, L2ONLY ? __ldcg(lkey + i) : lkey[i], k);
-    int msum = 0, psum = 0, shift = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      msum += ca[d] * k[d];
-      psum += ct[d] * k[d];
-      if (d == j - 1) shift = sh.c[d] * k[d];
-    }
-    const int m = fmod_(msum, sh.fL);
-    int q = fmod_(psum, sh.fL) + shift;
-    if (q >= L) q -= L;
-    const float2 v = cmulc(L2ONLY ? __ldcg(la + i) : la[i], tw[q]);
-    atomicAdd(&bins[m].x, -v.x);
-    atomicAdd(&bins[m].y, -v.y);
-  }
-}
-
-// One signal per cluster (grid = batch clusters of D+1 CTAs, in the longest-first order).
-template <int D, int MAXT, bool GS>
-__global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  __shared__ int s_count, s_ovf, s_n;
-  __shared__ int s_t0[2];                     // line-0 bins passing T0, by iteration parity
-  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
-  __shared__ unsigned char* s_base[kMaxD + 1];  // each rank's dynamic shared memory (generic address)
-
-  const int rank = (int)cluster.block_rank();
-  const int b = A.tab.order[blockIdx.x / (D + 1)];
-  const int si = A.tab.sig_shape[b];
-  const bool pf = A.prefetch != 0;
-  const int hash_cap = 1 << A.hash_bits;
-  const CLayout lay = recover_layout_c(D, A.L_max, A.k_cap, hash_cap, pf, GS);
-  float2* bufA = reinterpret_cast<float2*>(smem + lay.bufA);
-  float2* bufB = reinterpret_cast<float2*>(smem + lay.bufB);
-  float2* bufC = reinterpret_cast<float2*>(smem + lay.bufC);
-  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
-  float2* stws = reinterpret_cast<float2*>(smem + lay.stw);
-  // GS: this signal's slice of global workspace holds the list, the index and the counter
-  unsigned char* ws = GS ? A.gm_ws + (size_t)(blockIdx.x / (D + 1)) * A.gm_stride : nullptr;
-  float2* g_la = reinterpret_cast<float2*>(ws);
-  int* g_lkey = reinterpret_cast<int*>(ws + (size_t)A.k_cap * sizeof(float2));
-  int* g_hkey = g_lkey + A.k_cap;
-  int* g_hidx = g_hkey + hash_cap;
-  int* g_count = g_hidx + hash_cap;
-  const float2* la = GS ? g_la : reinterpret_cast<const float2*>(smem + lay.la);
-  const int* lkey = GS ? g_lkey : reinterpret_cast<const int*>(smem + lay.lkey);
-
-  load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
-  {
-    const int L = A.tab.shapes[si].L;
-    const float2* t = A.tab.twiddles + A.tab.shapes[si].stw_off;
-    for (int i = threadIdx.x; i < L - 1; i += blockDim.x) stws[i] = t[i];
-  }
-  if (threadIdx.x <= D) s_base[threadIdx.x] = cluster.map_shared_rank(smem, (int)threadIdx.x);
-  if (GS) {   // every rank clears a (D+1)-th of the global index
-    const int hcs = (hash_cap + D) / (D + 1);
-    const int h1 = min(hash_cap, (rank + 1) * hcs);
-    for (int i = rank * hcs + threadIdx.x; i < h1; i += blockDim.x) g_hkey[i] = kEmpty;
-    if (rank == 0 && threadIdx.x == 0) *g_count = 0;
-  } else {
-    int* hk = reinterpret_cast<int*>(smem + lay.hkey);
-    for (int i = threadIdx.x; i < lay.hc; i += blockDim.x) hk[i] = kEmpty;
-  }
-  if (threadIdx.x == 0) {
-    s_count = 0;
-    s_ovf = 0;
-    s_t0[0] = 0;
-    s_t0[1] = 0;
-  }
-  cluster.sync();   // every CTA started and initialised before any remote access
-
-  int* c_count = GS ? g_count : cluster.map_shared_rank(&s_count, 0);
-  int* c_ovf = cluster.map_shared_rank(&s_ovf, 0);
-  int* c_t0 = cluster.map_shared_rank(s_t0, 0);
-  const float2* x = A.cubes + A.offsets[b];
-  int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
-  float2* oa_out = A.out_a + (size_t)b * A.k_cap;
-
-  if (A.init_count != nullptr) {   // resume from a given set (rank 0 inserts into every replica)
-    if (rank == 0) {
-      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
-      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-        int k[D];
-        int key = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          k[d] = ok_out[i * D + d];
-          key += k[d] * sh.strides[d];
-        }
-        const bool ok = !on_grid<D>(sh, k) ||
-                        (GS ? cluster_insert_g<D>(g_la, g_lkey, g_hkey, g_hidx, g_count, A.k_cap, A.hash_bits, key, oa_out[i])
-                            : cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, oa_out[i]));
-        if (!ok) atomicOr(c_ovf, 1);
-      }
-    }
-    cluster.sync();
-  }
-  int n_set = min(GS ? __ldcg(g_count) : *c_count, A.k_cap);
-  const bool stop = *c_ovf != 0;
-
-  const int L = sh.L;
-  const int chunk = (L + D) / (D + 1);
-  const int m_lo = rank * chunk;
-  const int m_hi = min(L, m_lo + chunk);
-  const int T = stop ? 0 : A.tab.sig_T[b];
-  const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
-  const int* sched_t = A.tau + (size_t)b * A.sched_stride;
-  if (pf && T > 0) gather_one_line<D, 0, true>(bufA, x, sh, sched_a, sched_t, rank);
-  int iters = 0;
-  for (int t = 0; t < T; ++t) {
-    const int par = t & 1;
-    const int* al = sched_a + t * D;
-    const int* ta = sched_t + t * D;
-    // slot par was last read after the decode barrier of iteration t-2, before every rank
-    // arrived at the peel barrier of t-1, which this rank has passed
-    if (rank == 0 && threadIdx.x == 0) s_t0[par] = 0;
-    if (threadIdx.x < D) {
-      const int d = threadIdx.x;
-      s_ca[d] = cmodL(sh, d, al[d]);
-      s_ct[d] = cmodL(sh, d, ta[d]);
-    }
-    float2* cur = (pf && (t & 1)) ? bufC : bufA;
-    if (pf) {
-      if (t + 1 < T) {
-        gather_one_line<D, 0, true>((t & 1) ? bufA : bufC, x, sh, al + D, ta + D, rank);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-    } else if (A.gather_mode == 2) {
-      gather_one_line<D, 1, false>(bufA, x, sh, al, ta, rank);
-    } else {
-      gather_one_line<D, 0, false>(bufA, x, sh, al, ta, rank);
-    }
-    __syncthreads();
-    float2* bins = fft_line(cur, bufB, sh, tws, stws, 1.0f / (float)L);
-    peel_line_keys<D, GS>(bins, sh, la, lkey, n_set, s_ca, s_ct, tws, rank);
-    cluster.sync();   // every line peeled
-
-    const size_t boff = reinterpret_cast<unsigned char*>(bins) - smem;
-    int my_t0 = 0;
-    bool my_ovf = false;
-    for (int m = m_lo + threadIdx.x; m < m_hi; m += blockDim.x) {
-      const float2 s0 = reinterpret_cast<const float2*>(s_base[0] + boff)[m];
-      float2 sd[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) sd[d] = reinterpret_cast<const float2*>(s_base[d + 1] + boff)[m];
-      int k[D];
-      bool counted = false;
-      int v = A.th.fp64_all ? kUndecided : classify_fp32<D>(s0, sd, sh, A.th, k, &counted);
-      if (v == kUndecided) {
-        bool c64 = false;
-        v = classify_fp64<D>(s0, sd, sh, A.th, k, &c64);
-        counted = c64;
-      }
-      my_t0 += counted ? 1 : 0;
-      if (v != kAccept) continue;
-      int msum = 0, psum = 0, key = 0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        msum += s_ca[d] * k[d];
-        psum += s_ct[d] * k[d];
-        key += k[d] * sh.strides[d];
-      }
-      if (fmod_(msum, sh.fL) != m) continue;                            // T3
-      const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tws, A.th.amp_average != 0);
-      const bool ok = GS ? cluster_insert_g<D>(g_la, g_lkey, g_hkey, g_hidx, g_count, A.k_cap, A.hash_bits, key, a)
-                         : cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, a);
-      if (!ok) my_ovf = true;
-    }
-    if (my_t0) atomicAdd(c_t0 + par, my_t0);
-    if (my_ovf) atomicOr(c_ovf, 1);
-    cluster.sync();   // every insert landed in every replica
-    n_set = min(GS ? __ldcg(g_count) : *c_count, A.k_cap);
-    iters = t + 1;
-    if ((A.early_stop && c_t0[par] == 0) || *c_ovf != 0) break;   // the same verdict on every rank
-  }
-  if (pf) cp_async_wait<0>();
-  cluster.sync();   // no rank reads another's shared memory past this point
-
-  if (rank != 0) return;
-  // output order: a bitmap of the grid points in the shared memory the set does not use (all of it
-  // with GS), else sorted (key, position) pairs
-  {
-    auto get = [&](int i, int& key, float2& a) -> bool {
-      a = GS ? __ldcg(la + i) : la[i];
-      if (!keep_amplitude(a, A.th)) return false;
-      key = GS ? __ldcg(lkey + i) : lkey[i];
-      return true;
-    };
-    auto put = [&](int r, int key, float2 a) {
-      int k[D];
-      key_to_k<D>(sh, key, k);
-#pragma unroll
-      for (int d = 0; d < D; ++d) ok_out[r * D + d] = k[d];
-      oa_out[r] = a;
-    };
-    if (emit_by_bitmap(n_set, sh.N, smem, GS ? lay.total : lay.la, &s_n, get, put)) {
-      if (threadIdx.x == 0) {
-        A.out_count[b] = s_n;
-        A.out_iters[b] = iters;
-        A.out_status[b] = s_ovf ? kStatusCapacity : 0;
-      }
-      return;
-    }
-  }
-  int P = 1;
-  while (P < A.k_cap) P <<= 1;
-  // sort buffers: the line buffers, free now, or (GS) the global index
-  int* skey = GS ? g_hkey : reinterpret_cast<int*>(smem + lay.sort);
-  int* sidx = GS ? g_hidx : skey + P;
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n_set; i += blockDim.x) {
-    if (keep_amplitude(GS ? __ldcg(la + i) : la[i], A.th)) {
-      const int pos = atomicAdd(&s_n, 1);
-      skey[pos] = GS ? __ldcg(lkey + i) : lkey[i];
-      sidx[pos] = i;
-    }
-  }
-  __syncthreads();
-  const int n = s_n;
-  sort_pairs(skey, sidx, n);
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int i = sidx[r];
-    int k[D];
-    key_to_k<D>(sh, skey[r], k);
-#pragma unroll
-    for (int d = 0; d < D; ++d) ok_out[r * D + d] = k[d];
-    oa_out[r] = GS ? __ldcg(la + i) : la[i];
-  }
-  if (threadIdx.x == 0) {
-    A.out_count[b] = n;
-    A.out_iters[b] = iters;
-    A.out_status[b] = s_ovf ? kStatusCapacity : 0;
-  }
-}
-
-// ---- projection / raw lines: one CTA per (signal, schedule row) --------------------------------
-struct ProjectArgs {
-  const float2* cubes;
-  const int64_t* offsets;
-  const int* alpha;
-  const int* tau;
-  int n_sched;
-  DeviceTables tab;
-  int batch;
-  int L_max;
-  int dft;
-  float2* out;      // [batch][n_sched][D+1][L_max]
-};
-
-template <int D>
-__global__ void __launch_bounds__(256) k_project(ProjectArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  float2* bufA = reinterpret_cast<float2*>(smem);
-  float2* bufB = bufA + (size_t)(D + 1) * A.L_max;
-  int loaded = -1;
-  const long long units = (long long)A.batch * A.n_sched;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    const int b = (int)(u / A.n_sched);
-    const int si = A.tab.sig_shape[b];
-    if (si != loaded) {
-      __syncthreads();
-      load_shape(sh, A.tab.shapes, si, nullptr, A.tab.twiddles, false);
-      loaded = si;
-      __syncthreads();
-    }
-    const int L = sh.L;
-    const int* al = A.alpha + u * D;
-    const int* ta = A.tau + u * D;
-    gather_lines<D>(bufA, A.cubes + A.offsets[b], sh, al, ta);
-    __syncthreads();
-    const float2* res = A.dft ? fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L) : bufA;
-    float2* o = A.out + u * (D + 1) * (long long)A.L_max;
-    for (int i = threadIdx.x; i < (D + 1) * A.L_max; i += blockDim.x) {
-      const int j = i / A.L_max, m = i - j * A.L_max;
-      o[i] = (m < L) ? res[j * L + m] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-  }
-}
-
-// ---- synthesis (+, overwrite / accumulate) and peel (-) ------------------------------------------
-struct SynthArgs {
-  const int* alpha;
-  const int* tau;
-  int n_sched;
-  DeviceTables tab;
-  int batch;
-  int L_max;
-  int k_cap;
-  const int* k;
-  const float2* a;
-  const int* count;
-  int accumulate;   // 0 overwrite, +1 add, -1 subtract
-  float2* bins;
-};
-
-template <int D>
-__global__ void __launch_bounds__(256) k_synth(SynthArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
-  float2* acc = reinterpret_cast<float2*>(smem);
-  int loaded = -1;
-  const long long units = (long long)A.batch * A.n_sched;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    const int b = (int)(u / A.n_sched);
-    const int si = A.tab.sig_shape[b];
-    __syncthreads();
-    if (si != loaded) {
-      load_shape(sh, A.tab.shapes, si, nullptr, A.tab.twiddles, false);
-      loaded = si;
-      __syncthreads();
-    }
-    const int L = sh.L;
-    const int* al = A.alpha + u * D;
-    const int* ta = A.tau + u * D;
-    if (threadIdx.x < D) {
-      const int d = threadIdx.x;
-      s_ca[d] = cmodL(sh, d, al[d]);
-      s_ct[d] = cmodL(sh, d, ta[d]);
-    }
-    float2* o = A.bins + u * (D + 1) * (long long)A.L_max;
-    for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
-      const int j = i / L, m = i - j * L;
-      acc[i] = A.accumulate ? o[j * A.L_max + m] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const float sign = A.accumulate < 0 ? -1.f : 1.f;
-    const int cnt = min(max(A.count[b], 0), A.k_cap);
-    const float2* tw = A.tab.twiddles + sh.tw_off;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      int k[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) k[d] = A.k[((size_t)b * A.k_cap + i) * D + d];
-      if (on_grid<D>(sh, k)) project_entry<D>(acc, L, sh, k, A.a[(size_t)b * A.k_cap + i], s_ca, s_ct, tw, sign);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < (D + 1) * A.L_max; i += blockDim.x) {
-      const int j = i / A.L_max, m = i - j * A.L_max;
-      o[i] = (m < L) ? acc[j * L + m] : make_float2(0.f, 0.f);
-    }
-  }
-}
-
-// ---- one iteration's decode + merge on bins in global memory (unfused form) ----------------------
-struct DecodeArgs {
-  const float2* bins;   // [batch][1][D+1][L_max]
-  const int* alpha;
-  const int* tau;
-  DeviceTables tab;
-  int batch;
-  int L_max;
-  int k_cap;
-  int hash_bits;
-  Thresholds th;
-  int* k;
-  float2* a;
-  int* count;
-  int* t0_count;
-  int* status;
-};
-
-template <int D>
-__global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  __shared__ int s_count, s_t0, s_ovf;
-  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
-  const int hash_cap = 1 << A.hash_bits;
-  SetView set;
-  set.la = reinterpret_cast<float2*>(smem);
-  set.lk = reinterpret_cast<int*>(set.la + A.k_cap);
-  set.lkey = set.lk + (size_t)D * A.k_cap;
-  set.hkey = set.lkey + A.k_cap;
-  set.hidx = set.hkey + hash_cap;
-  set.count = &s_count;
-  set.k_cap = A.k_cap;
-  set.hash_bits = A.hash_bits;
-  for (int b = blockIdx.x; b < A.batch; b += gridDim.x) {
-    __syncthreads();
-    load_shape(sh, A.tab.shapes, A.tab.sig_shape[b], nullptr, A.tab.twiddles, false);
-    for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) set.hkey[i] = kEmpty;
-    if (threadIdx.x == 0) {
-      s_count = 0;
-      s_t0 = 0;
-      s_ovf = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x < D) {
-      const int d = threadIdx.x;
-      s_ca[d] = cmodL(sh, d, A.alpha[b * D + d]);
-      s_ct[d] = cmodL(sh, d, A.tau[b * D + d]);
-    }
-    const int n0 = min(max(A.count[b], 0), A.k_cap);
-    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-      int k[D];
-      int key = 0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        k[d] = A.k[((size_t)b * A.k_cap + i) * D + d];
-        key += k[d] * sh.strides[d];
-      }
-      if (on_grid<D>(sh, k)) set_insert<D>(set, k, key, A.a[(size_t)b * A.k_cap + i]);
-    }
-    __syncthreads();
-    decode_bins<D>(A.bins + (size_t)b * (D + 1) * A.L_max, A.L_max, sh, set, s_ca, s_ct,
-                   A.tab.twiddles + sh.tw_off, A.th, &s_t0, &s_ovf);
-    __syncthreads();
-    const int cnt = min(s_count, A.k_cap);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-#pragma unroll
-      for (int d = 0; d < D; ++d) A.k[((size_t)b * A.k_cap + i) * D + d] = set.lk[d * A.k_cap + i];
-      A.a[(size_t)b * A.k_cap + i] = set.la[i];
-    }
-    if (threadIdx.x == 0) {
-      A.count[b] = cnt;
-      A.t0_count[b] = s_t0;
-      if (s_ovf) A.status[b] |= kStatusCapacity;
-    }
-  }
-}
-
-// ---- finalize: drop small amplitudes and sort (unfused form) -------------------------------------
-struct FinalizeArgs {
-  DeviceTables tab;
-  int batch;
-  int k_cap;
-  int sort_cap;     // power of two >= k_cap
-  Thresholds th;
-  int* k;
-  float2* a;
-  int* count;
-};
-
-template <int D>
-__global__ void __launch_bounds__(256) k_finalize(FinalizeArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  __shared__ int s_n;
-  SetView set;
-  set.la = reinterpret_cast<float2*>(smem);
-  set.lk = reinterpret_cast<int*>(set.la + A.k_cap);
-  set.lkey = set.lk + (size_t)D * A.k_cap;
-  int* skey = set.lkey + A.k_cap;
-  int* sidx = skey + A.sort_cap;
-  set.k_cap = A.k_cap;
-  for (int b = blockIdx.x; b < A.batch; b += gridDim.x) {
-    __syncthreads();
-    load_shape(sh, A.tab.shapes, A.tab.sig_shape[b], nullptr, A.tab.twiddles, false);
-    __syncthreads();
-    const int n0 = min(max(A.count[b], 0), A.k_cap);
-    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-      int key = 0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const int kd = A.k[((size_t)b * A.k_cap + i) * D + d];
-        set.lk[d * A.k_cap + i] = kd;
-        key += kd * sh.strides[d];
-      }
-      set.lkey[i] = key;
-      set.la[i] = A.a[(size_t)b * A.k_cap + i];
-    }
-    __syncthreads();
-    sort_kept(set, n0, A.th, skey, sidx, &s_n);
-    const int n = s_n;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const int i = sidx[r];
-#pragma unroll
-      for (int d = 0; d < D; ++d) A.k[((size_t)b * A.k_cap + r) * D + d] = set.lk[d * A.k_cap + i];
-      A.a[(size_t)b * A.k_cap + r] = set.la[i];
-    }
-    if (threadIdx.x == 0) A.count[b] = n;
-  }
-}
-
-// ---- adjoints --------------------------------------------------------------------------------
-struct AdjProjectArgs {
-  const float2* g;         // [batch][n_sched][D+1][L_max]
-  const int64_t* offsets;
-  const int* alpha;
-  const int* tau;
-  int n_sched;
-  DeviceTables tab;
-  int batch;
-  int L_max;
-  float2* grad;            // cube layout
-};
-
-template <int D>
-__global__ void __launch_bounds__(256) k_adjoint_project(AdjProjectArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shape sh;
-  float2* bufA = reinterpret_cast<float2*>(smem);
-  float2* bufB = bufA + (size_t)(D + 1) * A.L_max;
-  int loaded = -1;
-  const long long units = (long long)A.batch * A.n_sched;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    const int b = (int)(u / A.n_sched);
-    const int si = A.tab.sig_shape[b];
-    if (si != loaded) {
-      __syncthreads();
-      load_shape(sh, A.tab.shapes, si, nullptr, A.tab.twiddles, false);
-      loaded = si;
-      __syncthreads();
-    }
-    const int L = sh.L;
-    const float2* g = A.g + u * (D + 1) * (long long)A.L_max;
-    for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
-      const int j = i / L, m = i - j * L;
-      const float2 v = g[j * A.L_max + m];
-      bufA[i] = make_float2(v.x, -v.y);          // conj(g)
-    }
-    __syncthreads();
-    // (1/L) sum_m g(m) exp(+j 2 pi l m / L) = conj( (1/L) DFT(conj g) )
-    const float2* res = fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L);
-    int al[D], ta[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      al[d] = fmod_(A.alpha[u * D + d] & 0x3fffffff, sh.fdims[d]);
-      ta[d] = fmod_(A.tau[u * D + d] & 0x3fffffff, sh.fdims[d]);
-    }
-    float2* out = A.grad + A.offsets[b];
-    for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
-      const int j = i / L, l = i - j * L;
-      const float2 v = res[i];
-      const int addr = line_address<D>(sh, al, ta, j, l);
-      atomicAdd(&out[addr].x, v.x);
-      atomicAdd(&out[addr].y, -v.y);
-    }
-    __syncthreads();
-  }
-}
-
-struct AdjSynthArgs {
-  const float2* g;         // [batch][n_sched][D+1][L_max]
-  const int* alpha;
-  const int* tau;
-  int n_sched;
-  DeviceTables tab;
-  int batch;
-  int L_max;
-  int k_cap;
-  const int* k;
-  const int* count;
-  float2* grad_a;          // [batch][k_cap]
-};
-
-template <int D>
-__global__ void __launch_bounds__(256) k_adjoint_synth(AdjSynthArgs A) {
-  const long long total = (long long)A.batch * A.k_cap;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / A.k_cap);
-    const int i = (int)(t - (long long)b * A.k_cap);
-    if (i >= min(max(A.count[b], 0), A.k_cap)) continue;
-    const Shape& sh = A.tab.shapes[A.tab.sig_shape[b]];
-    const int L = sh.L;
-    const float2* tw = A.tab.twiddles + sh.tw_off;
-    int k[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) k[d] = A.k[((size_t)b * A.k_cap + i) * D + d];
-    float2 acc = make_float2(0.f, 0.f);
-    for (int s = 0; s < A.n_sched && on_grid<D>(sh, k); ++s) {
-      const long long u = (long long)b * A.n_sched + s;
-      long long msum = 0, psum = 0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        msum += (long long)cmodL(sh, d, A.alpha[u * D + d]) * k[d];
-        psum += (long long)cmodL(sh, d, A.tau[u * D + d]) * k[d];
-      }
-      const int m = (int)(msum % L);
-      const int p = (int)(psum % L);
-      const float2* g = A.g + u * (D + 1) * (long long)A.L_max;
-      acc = cadd(acc, cmul(tw[p], g[m]));      // conj(W^p) = tw[p]
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        int q = p + sh.c[d] * k[d];
-        if (q >= L) q -= L;
-        acc = cadd(acc, cmul(tw[q], g[(d + 1) * A.L_max + m]));
-      }
-    }
-    A.grad_a[(size_t)b * A.k_cap + i] = acc;
-  }
-}
+#include "recover_common.cuh"
+#include "recover_shared.cuh"
+#include "recover_warp.cuh"
+#include "recover_cluster.cuh"
+#include "aux_kernels.cuh"
 
 // ================================================================================================
 // Host side: plan

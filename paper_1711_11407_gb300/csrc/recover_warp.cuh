@@ -1,0 +1,316 @@
+// The register-FFT recovery kernel k_recover_w (one warp per line, L in {32, 64, 128, 256}).
+// Part of the FPS-SFT recovery library for GB300 (sm_103a), arXiv 1711.11407; included by fpssft.cu.
+#pragma once
+
+#include "recover_common.cuh"
+
+// ---- warp-per-line variant for L = 32 R (R = 1, 2, 4, 8) ----------------------------------------
+// One CTA of D+1 warps per signal; warp j gathers line j straight into registers and transforms it
+// with warp_fft (no shared-memory staging, no CTA barrier inside the FFT).  Shared memory holds
+// only the bins (bank-swizzled), the twiddles and the bucket set, so several times more signals
+// are resident per SM than with the shared-memory Stockham path.
+struct WLayout {
+  size_t bins, tw, head, la, lk, nxt, stg, total;
+};
+
+static __host__ __device__ WLayout recover_layout_w(int D, int L_max, int k_cap, bool staged = false) {
+  auto al = [](size_t v) -> size_t { return (v + 15) & ~size_t(15); };
+  size_t P = 1;
+  while (P < (size_t)k_cap) P <<= 1;
+  const size_t lines = (size_t)(D + 1) * L_max * sizeof(float2);
+  const size_t sortb = 2 * P * sizeof(int);
+  WLayout w{};
+  size_t off = 0;
+  w.bins = off; off = al(off + (lines > sortb ? lines : sortb));
+  w.tw = off; off = al(off + (size_t)L_max * sizeof(float2));
+  w.head = off; off = al(off + (size_t)L_max * sizeof(int));
+  w.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
+  w.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
+  w.nxt = off; off = al(off + (size_t)k_cap * sizeof(int));
+  w.stg = off; off = al(off + (staged ? lines : 0));
+  w.total = off;
+  return w;
+}
+
+template <int D, int R>
+__device__ __forceinline__ void fft_store_w(float2 (&v)[R], float2* bins, const Shape& sh, const float2* tw, int j,
+                                            int lane, float invL) {
+  warp_fft<R>(v, tw, sh.L, lane);
+  const int br = brev5(lane);
+  float2* out = bins + j * sh.L;
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) out[swz(k2 + R * br)] = cscale(v[k2], invL);
+}
+
+// Sanitised slope and offset of schedule row t (every entry reduced into [0, N_d)).
+template <int D>
+__device__ __forceinline__ void sched_row(const Shape& sh, const int* al, const int* ta, int* alr, int* tar) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    alr[d] = fmod_(__ldg(al + d) & 0x3fffffff, sh.fdims[d]);
+    tar[d] = fmod_(__ldg(ta + d) & 0x3fffffff, sh.fdims[d]);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void peel_set_w(float2* bins, const Shape& sh, const BucketSet& s, int count, const int* ca,
+                                           const int* ct, const float2* __restrict__ tw) {
+  const int L = sh.L;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int k[D];
+    int msum = 0, psum = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      k[d] = s.lk[d * s.k_cap + i];
+      msum += ca[d] * k[d];
+      psum += ct[d] * k[d];
+    }
+    const int m = fmod_(msum, sh.fL);
+    const int p = fmod_(psum, sh.fL);
+    s.nxt[i] = atomicExch(&s.head[m], i);
+    const float2 a = s.la[i];
+    const int pm = swz(m);
+    float2 v = cmulc(a, tw[p]);
+    atomicAdd(&bins[pm].x, -v.x);
+    atomicAdd(&bins[pm].y, -v.y);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      int q = p + sh.c[d] * k[d];
+      if (q >= L) q -= L;
+      v = cmulc(a, tw[q]);
+      atomicAdd(&bins[(d + 1) * L + pm].x, -v.x);
+      atomicAdd(&bins[(d + 1) * L + pm].y, -v.y);
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& sh, const BucketSet& s, const int* ca,
+                                              const int* ct, const float2* __restrict__ tw, const Thresholds& th,
+                                              int* t0, int* ovf, int* accepted) {
+  const int L = sh.L;
+  int my_t0 = 0, my_acc = 0;
+  bool my_ovf = false;
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    const int pm = swz(m);
+    const float2 s0 = bins[pm];
+    float2 sd[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) sd[d] = bins[(d + 1) * L + pm];
+    int k[D];
+    bool counted = false;
+    int v = th.fp64_all ? kUndecided : classify_fp32<D>(s0, sd, sh, th, k, &counted);
+    if (v == kUndecided) {
+      bool c64 = false;
+      v = classify_fp64<D>(s0, sd, sh, th, k, &c64);
+      counted = c64;
+    }
+    my_t0 += counted ? 1 : 0;
+    if (v != kAccept) continue;
+    int msum = 0, psum = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      msum += ca[d] * k[d];
+      psum += ct[d] * k[d];
+    }
+    if (fmod_(msum, sh.fL) != m) continue;                            // T3
+    const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tw, th.amp_average != 0);
+    ++my_acc;
+    if (!bucket_insert<D>(s, m, k, a)) my_ovf = true;
+  }
+  if (my_t0) atomicAdd(t0, my_t0);
+  if (my_acc) atomicAdd(accepted, my_acc);
+  if (my_ovf) atomicOr(ovf, 1);
+}
+
+template <int D>
+__device__ __forceinline__ void sort_kept_w(const BucketSet& s, const Shape& sh, int count, const Thresholds& th,
+                                            int* skey, int* sidx, int* n_out) {
+  if (threadIdx.x == 0) *n_out = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    if (keep_amplitude(s.la[i], th)) {
+      int key = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) key += s.lk[d * s.k_cap + i] * sh.strides[d];
+      const int pos = atomicAdd(n_out, 1);
+      skey[pos] = key;
+      sidx[pos] = i;
+    }
+  }
+  __syncthreads();
+  sort_pairs(skey, sidx, *n_out);
+}
+
+// When every bin that passed T0 in iteration t-1 was decoded and merged, the set is most likely
+// complete and iteration t will find nothing (the early stop): iteration t then does not prefetch
+// t+1.  If the guess is wrong, iteration t+1 gathers its samples synchronously; the results do not
+// depend on the guess.
+template <int D, int R, bool STAGED>
+__device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
+                                         const float2* tws, float2* stg, const float2* __restrict__ x,
+                                         const int* sched_a, const int* sched_t, int T, int warp, int lane,
+                                         float invL, int* s_ca, int* s_ct, int* s_t0, int* s_ovf, int* s_acc) {
+  const int L = sh.L;
+  float2 nxt[STAGED ? 1 : R];
+  float2* my_stg = stg + warp * L;
+  bool have_next = false;      // samples of the current iteration already requested
+  bool likely_done = false;    // every T0 bin of the previous iteration was accepted
+  if (T > 0) {
+    int alr[D], tar[D];
+    sched_row<D>(sh, sched_a, sched_t, alr, tar);
+    if (STAGED)
+      gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
+    else
+      gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
+    have_next = true;
+  }
+  int iters = 0;
+  for (int t = 0; t < T; ++t) {
+    const int* al = sched_a + t * D;
+    const int* ta = sched_t + t * D;
+    if (threadIdx.x < D) {
+      const int d = threadIdx.x;
+      s_ca[d] = cmodL(sh, d, al[d]);
+      s_ct[d] = cmodL(sh, d, ta[d]);
+    }
+    for (int m = threadIdx.x; m < L; m += blockDim.x) set.head[m] = -1;
+    float2 v[R];
+    if (!have_next) {
+      int alr[D], tar[D];
+      sched_row<D>(sh, al, ta, alr, tar);
+      gather_line_regs<D, R>(v, x, sh, alr, tar, warp, lane);
+    } else if (STAGED) {
+      cp_async_wait<0>();
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = my_stg[lane + 32 * i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = nxt[STAGED ? 0 : i];
+    }
+    fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
+    have_next = t + 1 < T && !likely_done;
+    if (have_next) {
+      int alr[D], tar[D];
+      sched_row<D>(sh, al + D, ta + D, alr, tar);
+      if (STAGED)
+        gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
+      else
+        gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *s_t0 = 0;
+      *s_acc = 0;
+    }
+    peel_set_w<D>(bins, sh, set, min(*set.count, A.k_cap), s_ca, s_ct, tws);
+    __syncthreads();
+    decode_bins_w<D>(bins, sh, set, s_ca, s_ct, tws, A.th, s_t0, s_ovf, s_acc);
+    __syncthreads();
+    iters = t + 1;
+    const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
+    if (stop) break;
+    likely_done = A.early_stop && *s_acc == *s_t0;
+  }
+  if (STAGED) cp_async_wait<0>();   // a copy issued past the last iteration lands before reuse
+  return iters;
+}
+
+#ifndef FPSSFT_W_THREADS_PER_SM
+#define FPSSFT_W_THREADS_PER_SM 640   // resident threads per SM the warp path's register budget targets
+#endif
+
+#ifndef FPSSFT_WS_THREADS_PER_SM
+#define FPSSFT_WS_THREADS_PER_SM 768   // same for the variant that stages the prefetch in shared memory
+#endif
+
+template <int D, bool STAGED>
+__global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_SM : FPSSFT_W_THREADS_PER_SM) / (32 * (D + 1)))
+    k_recover_w(RecoverArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shape sh;
+  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n, s_acc;
+  __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+  const WLayout lay = recover_layout_w(D, A.L_max, A.k_cap, STAGED);
+  float2* bins = reinterpret_cast<float2*>(smem + lay.bins);
+  float2* tws = reinterpret_cast<float2*>(smem + lay.tw);
+  float2* stg = reinterpret_cast<float2*>(smem + lay.stg);
+  BucketSet set;
+  set.lk = reinterpret_cast<int*>(smem + lay.lk);
+  set.la = reinterpret_cast<float2*>(smem + lay.la);
+  set.head = reinterpret_cast<int*>(smem + lay.head);
+  set.nxt = reinterpret_cast<int*>(smem + lay.nxt);
+  set.count = &s_count;
+  set.k_cap = A.k_cap;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+
+  int loaded = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
+    __syncthreads();
+    const int qi = s_sig;
+    if (qi >= A.batch) break;
+    const int b = A.tab.order[qi];
+    const int si = A.tab.sig_shape[b];
+    if (si != loaded) {
+      load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, true);
+      loaded = si;
+    }
+    if (threadIdx.x == 0) {
+      s_count = 0;
+      s_ovf = 0;
+    }
+    __syncthreads();
+    const int L = sh.L;
+    const int R = L >> 5;
+    const float invL = 1.0f / (float)L;
+    const float2* x = A.cubes + A.offsets[b];
+    int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
+    float2* oa_out = A.out_a + (size_t)b * A.k_cap;
+
+    if (A.init_count != nullptr) {   // resume: the caller's set is appended as given
+      const int n0 = min(max(A.init_count[b], 0), A.k_cap);
+      for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        int k[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) k[d] = ok_out[i * D + d];
+        if (!on_grid<D>(sh, k)) continue;
+        const int idx = atomicAdd(&s_count, 1);
+#pragma unroll
+        for (int d = 0; d < D; ++d) set.lk[d * A.k_cap + idx] = k[d];
+        set.la[idx] = oa_out[i];
+      }
+      __syncthreads();
+    }
+
+    const int T = A.tab.sig_T[b];
+    const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
+    const int* sched_t = A.tau + (size_t)b * A.sched_stride;
+    int iters = 0;
+    switch (R) {
+      case 1: iters = iterate_w<D, 1, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 2: iters = iterate_w<D, 2, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+    }
+
+    const int count = min(s_count, A.k_cap);
+    int* skey = reinterpret_cast<int*>(bins);
+    int* sidx = skey + (lay.tw - lay.bins) / (2 * sizeof(int));
+    sort_kept_w<D>(set, sh, count, A.th, skey, sidx, &s_n);
+    const int n = s_n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int i = sidx[r];
+#pragma unroll
+      for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
+      oa_out[r] = set.la[i];
+    }
+    if (threadIdx.x == 0) {
+      A.out_count[b] = n;
+      A.out_iters[b] = iters;
+      A.out_status[b] = s_ovf ? kStatusCapacity : 0;
+    }
+    __syncthreads();
+  }
+}
