@@ -233,3 +233,25 @@ def test_cluster_path_global_set_resume_equals_one_run():
     k1, a1 = ref.signal(0)
     k2, a2 = out.signal(0)
     assert np.array_equal(k1, k2) and np.allclose(a1, a2, rtol=AMP_TOL, atol=0)
+
+
+@pytest.mark.parametrize("kcap", [640, 20000])
+def test_cluster_path_host_buffers_and_pinned_in_place_reads_equal_device_buffers(kcap):
+    """fpssft_recover_host (host buffers copied in and out) and the in-place read of pinned host
+    cubes give the device-buffer sets on the cluster path (set in shared memory and in global
+    workspace)."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("single_240x256")
+    plan = Plan(wl.dims, configs.params_for(wl, fft_path=3, k_cap=kcap))
+    assert plan.info["fft_path"] == 3 and plan.info["global_workspace"] == (1 if kcap > 640 else 0)
+    cubes, offs, al, ta = to_dev(wl)
+    ref = plan.recover(cubes, offs, al, ta)
+    torch.cuda.synchronize()
+    hv = plan.recover_host(wl.cubes, wl.offsets, wl.alpha, wl.tau)
+    mp = plan.recover_mapped(torch.from_numpy(wl.cubes).pin_memory(), offs, al, ta)
+    torch.cuda.synchronize()
+    n = int(ref.count[0])
+    for got in (hv, mp):
+        assert int(got.count[0]) == n and int(got.iters[0]) == int(ref.iters[0])
+        assert torch.equal(got.k[0, :n].cpu(), ref.k[0, :n].cpu())
+        assert torch.allclose(got.a[0, :n].cpu(), ref.a[0, :n].cpu(), rtol=AMP_TOL, atol=0)
