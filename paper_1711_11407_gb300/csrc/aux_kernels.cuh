@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(256) k_project(ProjectArgs A) {
     const int* ta = A.tau + u * D;
     gather_lines<D>(bufA, A.cubes + A.offsets[b], sh, al, ta);
     __syncthreads();
-    const float2* res = A.dft ? fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L) : bufA;
+    const float2* stw = sh.stw_off < 0 ? nullptr : A.tab.twiddles + sh.stw_off;
+    const float2* res = A.dft ? fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L, stw) : bufA;
     float2* o = A.out + u * (D + 1) * (long long)A.L_max;
     for (int i = threadIdx.x; i < (D + 1) * A.L_max; i += blockDim.x) {
       const int j = i / A.L_max, m = i - j * A.L_max;
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(256) k_adjoint_project(AdjProjectArgs A) {
     }
     __syncthreads();
     // (1/L) sum_m g(m) exp(+j 2 pi l m / L) = conj( (1/L) DFT(conj g) )
-    const float2* res = fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L);
+    const float2* res = fft_lines(bufA, bufB, D + 1, sh, A.tab.twiddles + sh.tw_off, 1.0f / (float)L,
+                                  sh.stw_off < 0 ? nullptr : A.tab.twiddles + sh.stw_off);
     int al[D], ta[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {

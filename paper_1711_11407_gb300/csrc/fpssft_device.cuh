@@ -277,10 +277,12 @@ __device__ __forceinline__ void butterfly<8>(float2 (&v)[8]) {
   }
 }
 
+// stw (may be null): the per-stage twiddle table of fft_line (entry i Ns + k - 1 = tw[i k tstep]),
+// read at consecutive addresses by consecutive butterflies instead of the strided tw reads.
 template <int R>
 __device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2* __restrict__ out, int L,
                                           int nlines, int Ns, int tstep, const FastDiv& fnb, const FastDiv& fns,
-                                          const float2* __restrict__ tw, float sc) {
+                                          const float2* __restrict__ tw, const float2* __restrict__ stw, float sc) {
   const int nb = fnb.d;
   const int total = nlines * nb;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
@@ -294,7 +296,7 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2*
     for (int i = 0; i < R; ++i) v[i] = src[j + i * nb];
     if (k != 0) {
 #pragma unroll
-      for (int i = 1; i < R; ++i) v[i] = cmul(v[i], tw[i * k * tstep]);
+      for (int i = 1; i < R; ++i) v[i] = cmul(v[i], stw ? stw[i * Ns + k - 1] : tw[i * k * tstep]);
     }
     butterfly<R>(v);
     const int base = (j - k) * R + k;
@@ -307,7 +309,8 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2*
 // from shared memory.
 __device__ __forceinline__ void fft_stage_generic(const float2* __restrict__ in, float2* __restrict__ out,
                                                   int L, int nlines, int Ns, int R, int tstep, const FastDiv& fnb,
-                                                  const FastDiv& fns, const float2* __restrict__ tw, float sc) {
+                                                  const FastDiv& fns, const float2* __restrict__ tw,
+                                                  const float2* __restrict__ stw, float sc) {
   const int nb = fnb.d;
   const int rstep = nb;              // exp(-j 2 pi x / R) = tw[(x mod R) * L / R]
   const int total = nlines * nb;
@@ -323,7 +326,7 @@ __device__ __forceinline__ void fft_stage_generic(const float2* __restrict__ in,
       int x = 0;                     // (i q) mod R, advanced incrementally
       for (int i = 0; i < R; ++i) {
         float2 v = src[j + i * nb];
-        if (k != 0 && i != 0) v = cmul(v, tw[i * k * tstep]);
+        if (k != 0 && i != 0) v = cmul(v, stw ? stw[i * Ns + k - 1] : tw[i * k * tstep]);
         acc = cadd(acc, cmul(v, tw[x * rstep]));
         x += q;
         if (x >= R) x -= R;
@@ -337,7 +340,8 @@ __device__ __forceinline__ void fft_stage_generic(const float2* __restrict__ in,
 // `scale` at the last stage; buf1 is the ping-pong partner.  Ends with a barrier after each stage
 // and returns the buffer holding the result.
 __device__ __forceinline__ float2* fft_lines(float2* buf0, float2* buf1, int nlines, const Shape& sh,
-                                             const float2* __restrict__ tw, float scale) {
+                                             const float2* __restrict__ tw, float scale,
+                                             const float2* __restrict__ stw = nullptr) {
   float2* in = buf0;
   float2* out = buf1;
   int Ns = 1;
@@ -347,12 +351,12 @@ __device__ __forceinline__ float2* fft_lines(float2* buf0, float2* buf1, int nli
     const int ts = sh.tstep[s];
     const float sc = (s == sh.nst - 1) ? scale : 1.f;
     switch (R) {
-      case 2: fft_stage<2>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
-      case 3: fft_stage<3>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
-      case 4: fft_stage<4>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
-      case 5: fft_stage<5>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
-      case 8: fft_stage<8>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
-      default: fft_stage_generic(in, out, L, nlines, Ns, R, ts, sh.fnb[s], sh.fns[s], tw, sc); break;
+      case 2: fft_stage<2>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, stw, sc); break;
+      case 3: fft_stage<3>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, stw, sc); break;
+      case 4: fft_stage<4>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, stw, sc); break;
+      case 5: fft_stage<5>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, stw, sc); break;
+      case 8: fft_stage<8>(in, out, L, nlines, Ns, ts, sh.fnb[s], sh.fns[s], tw, stw, sc); break;
+      default: fft_stage_generic(in, out, L, nlines, Ns, R, ts, sh.fnb[s], sh.fns[s], tw, stw, sc); break;
     }
     __syncthreads();
     float2* t = in;

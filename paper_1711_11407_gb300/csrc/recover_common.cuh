@@ -48,7 +48,7 @@ struct RecoverArgs {
 };
 
 struct SmemLayout {
-  size_t bufA, bufB, bufC, tw, la, lk, lkey, hkey, hidx, total;
+  size_t bufA, bufB, bufC, tw, stw, la, lk, lkey, hkey, hidx, total;
 };
 
 // bufA / bufC: the samples of iterations t and t+1 (bufC only when the gather is prefetched);
@@ -63,6 +63,7 @@ static __host__ __device__ SmemLayout recover_layout(int D, int L_max, int k_cap
   s.bufB = off; off = al(off + lines);
   s.bufC = off; off = al(off + (prefetch ? lines : 0));
   s.tw = off; off = al(off + (tw_smem ? (size_t)L_max * sizeof(float2) : 0));
+  s.stw = off; off = al(off + (tw_smem ? (size_t)L_max * sizeof(float2) : 0));   // per-stage twiddles
   s.la = off; off = al(off + (size_t)k_cap * sizeof(float2));
   s.lk = off; off = al(off + (size_t)D * k_cap * sizeof(int));
   s.lkey = off; off = al(off + (size_t)k_cap * sizeof(int));

@@ -8,8 +8,11 @@
 // GM = true: the same kernel with the lines, the FFT partner and the recovered set in a per-CTA
 // slice of global workspace (L2-resident) instead of shared memory, for lines or sets too large
 // for one CTA's shared memory.  All device functions take generic pointers.
+// Register budget: the 512-thread instance for D <= 2 keeps 64 registers so that two CTAs share an
+// SM when shared memory allows (mid-length lines in large batches); for D >= 3 the longer decode
+// needs more registers (at 64 it spills: the 64^3 batch ran twice as long).
 template <int D, int MAXT, bool GM = false>
-__global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
+__global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recover(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
@@ -22,6 +25,7 @@ __global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
   float2* bufC = reinterpret_cast<float2*>(base + lay.bufC);
   const bool pf = A.prefetch != 0;
   float2* tws = reinterpret_cast<float2*>(base + lay.tw);
+  float2* stws = reinterpret_cast<float2*>(base + lay.stw);
   SetView set;
   set.la = reinterpret_cast<float2*>(base + lay.la);
   set.lk = reinterpret_cast<int*>(base + lay.lk);
@@ -43,6 +47,11 @@ __global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
     const int si = A.tab.sig_shape[b];
     if (si != loaded) {
       load_shape(sh, A.tab.shapes, si, tws, A.tab.twiddles, A.tw_smem != 0);
+      const int so = A.tab.shapes[si].stw_off;
+      if (A.tw_smem && so >= 0) {
+        const int L = A.tab.shapes[si].L;
+        for (int i = threadIdx.x; i < L - 1; i += blockDim.x) stws[i] = A.tab.twiddles[so + i];
+      }
       loaded = si;
     }
     for (int i = threadIdx.x; i < hash_cap; i += blockDim.x) set.hkey[i] = kEmpty;
@@ -52,6 +61,7 @@ __global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
     }
     __syncthreads();
     const float2* tw = A.tw_smem ? tws : A.tab.twiddles + sh.tw_off;
+    const float2* stw = sh.stw_off < 0 ? nullptr : (A.tw_smem ? stws : A.tab.twiddles + sh.stw_off);
     const int L = sh.L;
     const float2* x = A.cubes + A.offsets[b];
     int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
@@ -101,7 +111,7 @@ __global__ void __launch_bounds__(MAXT) k_recover(RecoverArgs A) {
       }
       __syncthreads();
       if (threadIdx.x == 0) s_t0 = 0;
-      float2* bins = fft_lines(cur, bufB, D + 1, sh, tw, 1.0f / (float)L);
+      float2* bins = fft_lines(cur, bufB, D + 1, sh, tw, 1.0f / (float)L, stw);
       peel_set<D>(bins, sh, set, min(s_count, A.k_cap), s_ca, s_ct, tw);
       __syncthreads();
       decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf);
