@@ -60,9 +60,18 @@ def candidates(dims, params: Params):
 
 
 def _time(plan, args, reps, flush):
+    """Mean launch time over at least `reps` launches; short launches get more of them (about 4 ms
+    of timed work, at most 50), so that candidates a few microseconds apart are told apart."""
     stream = torch.cuda.current_stream()
     plan.recover(*args)
     stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.recover(*args)
+    e1.record(stream)
+    e1.synchronize()
+    first = max(e0.elapsed_time(e1), 1e-3)
+    reps = max(reps, min(50, int(math.ceil(4.0 / first))))
     total = 0.0
     for _ in range(reps):
         flush.zero_()
