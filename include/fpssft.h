@@ -111,8 +111,10 @@ typedef struct {
   int prefetch;       /* 1: the next iteration's lines are gathered while the current one computes */
   int fft_path;       /* 1: shared-memory FFT, one CTA per signal; 2: register FFT, one warp per line;
                          3: one CTA per line, a cluster of D+1 CTAs per signal (grid = batch (D+1)) */
-  int global_workspace; /* 1: lines and recovered set too large for shared memory live in a
-                        per-CTA slice of plan-owned global workspace (fpssft_recover only) */
+  int global_workspace; /* 1: data too large for shared memory lives in plan-owned global
+                        workspace (fpssft_recover only): on path 1 the lines and the recovered set
+                        (one slice per persistent CTA), on path 3 the recovered set (one slice per
+                        signal, 12 bytes per set entry + 8 bytes per index slot) */
 } fpssft_plan_info;
 
 /* Create a plan for `batch` signals of dimension D with shapes dims (HOST int64 [batch][D],
@@ -120,8 +122,9 @@ typedef struct {
  * every distinct L, FP64-derived twiddle tables, the per-signal iteration budget and a
  * longest-first work order, and uploads them to device workspace owned by the plan.
  * When the D+1 lines or the recovered set do not fit one CTA's shared memory, fpssft_recover keeps
- * them in plan-owned global workspace (2 x SM count slices); fpssft_project, fpssft_lines,
- * fpssft_synth and fpssft_adjoint then return FPSSFT_ERR_UNSUPPORTED for that plan.
+ * them in plan-owned global workspace (2 x SM count slices on path 1; on path 3 only the set, one
+ * slice per signal); fpssft_project, fpssft_lines, fpssft_synth and fpssft_adjoint return
+ * FPSSFT_ERR_UNSUPPORTED for a plan whose D+1 lines exceed shared memory.
  * Must be called with the target device current. */
 fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch, const int64_t* dims,
                                  const fpssft_params* params);
