@@ -42,7 +42,7 @@ UNIT = "signals/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fpssft", choices=["fpssft", "reference"])
     ap.add_argument("--workload", default="uneven_2d")
