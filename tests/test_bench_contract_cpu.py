@@ -1,0 +1,39 @@
+"""The benchmark's CPU-side contract (no GPU): the reference arm's JSON line and the kernel-source
+hash that decides whether a committed DRAM-traffic record still applies."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--workload", "single_128x128"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "signals/s" and d["higher_is_better"] is True
+    assert d["metric"] == bench.METRIC and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "signals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "single_128x128"
+
+
+def test_source_hash_ignores_comments_and_whitespace_but_not_code():
+    a = "int f(int x) {  // twice\n  return 2 * x; /* done */ }\n"
+    b = "int f(int x) { return 2 * x; }"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments(a) != bench.strip_comments(c)
+    assert bench.strip_comments('const char* s = "// kept"; // dropped') == 'const char* s = "// kept";'
+    h = bench.source_hash()
+    assert len(h) == 16 and h == bench.source_hash()
