@@ -904,6 +904,66 @@ __device__ __forceinline__ bool emit_by_bitmap(int count, int N, unsigned char* 
   return true;
 }
 
+constexpr int kOutBuckets = 64;
+
+// Output of the kept entries (|a| > theta0, a = amp_of(i)) in order of linear index by a bucket
+// sort on the key's top bits (keys < N <= 2^nb, bucket = key >> (nb - 6)): a count per bucket, an
+// exclusive scan of the 64 counts by one warp, a scatter into bucket order, and the rank of each
+// key inside its bucket by counting the bucket's smaller keys; put(r, i) writes output row r from
+// entry i.  tkey / tidx need `count` ints each, s_cnt / s_off kOutBuckets ints.  Returns the
+// number written.
+template <typename AmpOf, typename KeyOf, typename Put>
+__device__ __forceinline__ int emit_bucketed(int count, int N, const Thresholds& th, int* tkey, int* tidx, int* s_cnt,
+                                             int* s_off, int* s_n, AmpOf amp_of, KeyOf key_of, Put put) {
+  const int tid = threadIdx.x;
+  const int bd = blockDim.x;
+  int nb = 0;
+  while ((1 << nb) < N) ++nb;
+  const int shift = nb > 6 ? nb - 6 : 0;
+  for (int q = tid; q < kOutBuckets; q += bd) s_cnt[q] = 0;
+  __syncthreads();
+  for (int i = tid; i < count; i += bd)
+    if (keep_amplitude(amp_of(i), th)) atomicAdd(&s_cnt[key_of(i) >> shift], 1);
+  __syncthreads();
+  if (tid < 32) {   // lane l scans buckets 2l and 2l + 1
+    const int c0 = s_cnt[2 * tid], c1 = s_cnt[2 * tid + 1];
+    int incl = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    const int excl = incl - (c0 + c1);
+    s_off[2 * tid] = excl;
+    s_off[2 * tid + 1] = excl + c0;
+    s_cnt[2 * tid] = 0;         // from here on: fill counters
+    s_cnt[2 * tid + 1] = 0;
+    if (tid == 31) *s_n = incl;
+  }
+  __syncthreads();
+  for (int i = tid; i < count; i += bd) {
+    if (keep_amplitude(amp_of(i), th)) {
+      const int key = key_of(i);
+      const int bk = key >> shift;
+      const int pos = s_off[bk] + atomicAdd(&s_cnt[bk], 1);
+      tkey[pos] = key;
+      tidx[pos] = i;
+    }
+  }
+  __syncthreads();
+  const int n = *s_n;
+  for (int p = tid; p < n; p += bd) {
+    const int key = tkey[p];
+    const int bk = key >> shift;
+    const int hi = bk + 1 < kOutBuckets ? s_off[bk + 1] : n;
+    int r = s_off[bk];
+    for (int q = s_off[bk]; q < hi; ++q) r += tkey[q] < key ? 1 : 0;
+    put(r, tidx[p]);
+  }
+  __syncthreads();
+  return n;
+}
+
 // Compact the entries with |a| > theta0 into (skey, sidx) and sort them by linear index: on return
 // *n_out is the number kept and sidx[r] the list position of the r-th smallest key.
 __device__ __forceinline__ void sort_kept(const SetView& s, int count, const Thresholds& th, int* skey, int* sidx,

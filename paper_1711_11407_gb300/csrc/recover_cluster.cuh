@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
   __shared__ int s_count, s_ovf, s_n;
+  __shared__ int s_cnt[kOutBuckets], s_off[kOutBuckets];
   __shared__ int s_t0[2];                     // line-0 bins passing T0, by iteration parity
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
   __shared__ unsigned char* s_base[kMaxD + 1];  // each rank's dynamic shared memory (generic address)
@@ -369,29 +370,19 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   }
   int P = 1;
   while (P < A.k_cap) P <<= 1;
-  // sort buffers: the line buffers, free now, or (GS) the global index
-  int* skey = GS ? g_hkey : reinterpret_cast<int*>(smem + lay.sort);
-  int* sidx = GS ? g_hidx : skey + P;
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n_set; i += blockDim.x) {
-    if (keep_amplitude(GS ? __ldcg(la + i) : la[i], A.th)) {
-      const int pos = atomicAdd(&s_n, 1);
-      skey[pos] = GS ? __ldcg(lkey + i) : lkey[i];
-      sidx[pos] = i;
-    }
-  }
-  __syncthreads();
-  const int n = s_n;
-  sort_pairs(skey, sidx, n);
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int i = sidx[r];
+  // otherwise a bucket sort; its buffers: the line buffers, free now, or (GS) the global index
+  int* tkey = GS ? g_hkey : reinterpret_cast<int*>(smem + lay.sort);
+  int* tidx = GS ? g_hidx : tkey + P;
+  auto amp_of = [&](int i) { return GS ? __ldcg(la + i) : la[i]; };
+  auto key_of = [&](int i) { return GS ? __ldcg(lkey + i) : lkey[i]; };
+  auto put_row = [&](int r, int i) {
     int k[D];
-    key_to_k<D>(sh, skey[r], k);
+    key_to_k<D>(sh, key_of(i), k);
 #pragma unroll
     for (int d = 0; d < D; ++d) ok_out[r * D + d] = k[d];
-    oa_out[r] = GS ? __ldcg(la + i) : la[i];
-  }
+    oa_out[r] = amp_of(i);
+  };
+  const int n = emit_bucketed(n_set, sh.N, A.th, tkey, tidx, s_cnt, s_off, &s_n, amp_of, key_of, put_row);
   if (threadIdx.x == 0) {
     A.out_count[b] = n;
     A.out_iters[b] = iters;

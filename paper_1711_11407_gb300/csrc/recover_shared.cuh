@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
   __shared__ Shape sh;
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
+  __shared__ int s_cnt[kOutBuckets], s_off[kOutBuckets];
 
   unsigned char* base = GM ? A.gm_ws + (size_t)blockIdx.x * A.gm_stride : smem;
   const SmemLayout lay = recover_layout(D, A.L_max, A.k_cap, 1 << A.hash_bits, A.tw_smem != 0, A.prefetch != 0);
@@ -122,16 +123,16 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
     }
 
     if (pf) cp_async_wait<0>();   // a prefetch past the last iteration still lands before reuse
-    // output: keep |a| > theta0, sorted by linear index (hash arrays reused as sort buffers)
+    // output: keep |a| > theta0, in order of linear index (hash arrays reused as sort buffers)
     const int count = min(s_count, A.k_cap);
-    sort_kept(set, count, A.th, set.hkey, set.hidx, &s_n);
-    const int n = s_n;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const int i = set.hidx[r];
+    auto key_of = [&](int i) { return set.lkey[i]; };
+    auto put = [&](int r, int i) {
 #pragma unroll
       for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
       oa_out[r] = set.la[i];
-    }
+    };
+    auto amp_of = [&](int i) { return set.la[i]; };
+    const int n = emit_bucketed(count, sh.N, A.th, set.hkey, set.hidx, s_cnt, s_off, &s_n, amp_of, key_of, put);
     if (threadIdx.x == 0) {
       A.out_count[b] = n;
       A.out_iters[b] = iters;

@@ -123,75 +123,6 @@ __device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& s
   if (my_ovf) atomicOr(ovf, 1);
 }
 
-constexpr int kOutBuckets = 64;
-
-// Writes the kept entries (|a| > theta0) to out_k / out_a in order of linear index by a bucket sort
-// on the key's top bits (keys < N <= 2^nb, bucket = key >> (nb - 6)): a count per bucket, an
-// exclusive scan of the 64 counts by one warp, a scatter into bucket order, and the rank of each
-// key inside its bucket by counting the bucket's smaller keys; every entry writes its own output
-// row.  tkey / tidx need `count` ints each.  Returns the number of entries written.
-template <int D>
-__device__ __forceinline__ int emit_bucketed_w(const BucketSet& s, const Shape& sh, int count, const Thresholds& th,
-                                               int* tkey, int* tidx, int* s_cnt, int* s_off, int* s_n, int* ok_out,
-                                               float2* oa_out) {
-  const int tid = threadIdx.x;
-  const int bd = blockDim.x;
-  int nb = 0;
-  while ((1 << nb) < sh.N) ++nb;
-  const int shift = nb > 6 ? nb - 6 : 0;
-  auto key_of = [&](int i) {
-    int key = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) key += s.lk[d * s.k_cap + i] * sh.strides[d];
-    return key;
-  };
-  for (int q = tid; q < kOutBuckets; q += bd) s_cnt[q] = 0;
-  __syncthreads();
-  for (int i = tid; i < count; i += bd)
-    if (keep_amplitude(s.la[i], th)) atomicAdd(&s_cnt[key_of(i) >> shift], 1);
-  __syncthreads();
-  if (tid < 32) {   // lane l scans buckets 2l and 2l + 1
-    const int c0 = s_cnt[2 * tid], c1 = s_cnt[2 * tid + 1];
-    int incl = c0 + c1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (tid >= o) incl += y;
-    }
-    const int excl = incl - (c0 + c1);
-    s_off[2 * tid] = excl;
-    s_off[2 * tid + 1] = excl + c0;
-    s_cnt[2 * tid] = 0;         // from here on: fill counters
-    s_cnt[2 * tid + 1] = 0;
-    if (tid == 31) *s_n = incl;
-  }
-  __syncthreads();
-  for (int i = tid; i < count; i += bd) {
-    if (keep_amplitude(s.la[i], th)) {
-      const int key = key_of(i);
-      const int bk = key >> shift;
-      const int pos = s_off[bk] + atomicAdd(&s_cnt[bk], 1);
-      tkey[pos] = key;
-      tidx[pos] = i;
-    }
-  }
-  __syncthreads();
-  const int n = *s_n;
-  for (int p = tid; p < n; p += bd) {
-    const int key = tkey[p];
-    const int bk = key >> shift;
-    const int hi = bk + 1 < kOutBuckets ? s_off[bk + 1] : n;
-    int r = s_off[bk];
-    for (int q = s_off[bk]; q < hi; ++q) r += tkey[q] < key ? 1 : 0;
-    const int i = tidx[p];
-#pragma unroll
-    for (int d = 0; d < D; ++d) ok_out[r * D + d] = s.lk[d * s.k_cap + i];
-    oa_out[r] = s.la[i];
-  }
-  __syncthreads();
-  return n;
-}
-
 // When every bin that passed T0 in iteration t-1 was decoded and merged, the set is most likely
 // complete and iteration t will find nothing (the early stop): iteration t then does not prefetch
 // t+1.  If the guess is wrong, iteration t+1 gathers its samples synchronously; the results do not
@@ -349,7 +280,19 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
     const int count = min(s_count, A.k_cap);
     int* tkey = reinterpret_cast<int*>(bins);                        // the bins are free now
     int* tidx = tkey + (lay.tw - lay.bins) / (2 * sizeof(int));
-    const int n = emit_bucketed_w<D>(set, sh, count, A.th, tkey, tidx, s_cnt, s_off, &s_n, ok_out, oa_out);
+    auto key_of = [&](int i) {
+      int key = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) key += set.lk[d * A.k_cap + i] * sh.strides[d];
+      return key;
+    };
+    auto put = [&](int r, int i) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) ok_out[r * D + d] = set.lk[d * A.k_cap + i];
+      oa_out[r] = set.la[i];
+    };
+    auto amp_of = [&](int i) { return set.la[i]; };
+    const int n = emit_bucketed(count, sh.N, A.th, tkey, tidx, s_cnt, s_off, &s_n, amp_of, key_of, put);
     if (threadIdx.x == 0) {
       A.out_count[b] = n;
       A.out_iters[b] = iters;
