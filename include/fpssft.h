@@ -270,6 +270,25 @@ fpssft_status fpssft_probe_gather(const void* buf, int64_t n_elems, int reads_pe
  * in *previous (nullable).  bytes < 0 only queries. */
 fpssft_status fpssft_l2_fetch_granularity(int bytes, int* previous);
 
+/* Tracing (no counterpart in the paper).  A library built with -DFPSSFT_PHASE_TIMERS (the Python
+ * package's `phases` module builds it as libfpssft_phases.so) times the phases of the three
+ * recovery kernels with the SM cycle counter: thread 0 of every CTA adds up the cycles between CTA
+ * barriers placed at the phase boundaries and, when the CTA ends, adds them to one device array.
+ * fpssft_phase_read waits for the device, copies that array into out (host, FPSSFT_PHASE_WORDS
+ * values) and clears it:
+ *   out[0 .. FPSSFT_PHASE_COUNT-1]  cycles per phase summed over CTAs, in the order setup,
+ *                                   gather, FFT, peel, decode (classify and merge), exchange (the
+ *                                   cluster barriers; cluster path only), output;
+ *   out[FPSSFT_PHASE_COUNT]         CTAs that contributed (each CTA of each launch once);
+ *   out[FPSSFT_PHASE_COUNT + 1]     recovery iterations those CTAs ran;
+ *   out[FPSSFT_PHASE_COUNT + 2]     their cycles from start to end of the kernel;
+ *   out[FPSSFT_PHASE_COUNT + 3]     the global-timer nanoseconds of the same spans.
+ * The barriers make a timed launch slower than a plain one; its results are the same.  The default
+ * build returns FPSSFT_ERR_UNSUPPORTED and touches nothing. */
+#define FPSSFT_PHASE_COUNT 7
+#define FPSSFT_PHASE_WORDS (FPSSFT_PHASE_COUNT + 4)
+fpssft_status fpssft_phase_read(int64_t* out);
+
 /* Message of the last failed call on this thread ("" when none). */
 const char* fpssft_last_error(void);
 

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libfpssft.so")
 SOURCES = [os.path.join(_HERE, "csrc", "fpssft.cu")]
 DEPENDS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("fpssft_device.cuh", "recover_common.cuh",
                                                                 "recover_shared.cuh", "recover_warp.cuh",
-                                                                "recover_cluster.cuh", "aux_kernels.cuh")] + \
+                                                                "recover_cluster.cuh", "aux_kernels.cuh",
+                                                                "phase_timers.cuh")] + \
     [os.path.join(_ROOT, "include", "fpssft.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--expt-relaxed-constexpr", "-shared", "-Xcompiler", "-fPIC"]
@@ -28,6 +29,7 @@ ADJ_PROJECT, ADJ_SYNTH = 0, 1
 
 _lock = threading.Lock()
 _lib = None
+_variant = None   # path of a build variant loaded instead of LIB_PATH (see use_library)
 
 
 class FpssftError(RuntimeError):
@@ -43,31 +45,33 @@ def _nvcc():
     return "nvcc"
 
 
-def needs_build():
-    if not os.path.exists(LIB_PATH):
+def needs_build(path=LIB_PATH):
+    if not os.path.exists(path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return any(os.path.getmtime(p) > t for p in DEPENDS)
 
 
-def build(force=False, verbose=False):
-    """Compile libfpssft.so for sm_103a next to this file (atomic rename)."""
-    if not force and not needs_build():
-        return LIB_PATH
+def build(force=False, verbose=False, out=LIB_PATH, defines=()):
+    """Compile the library for sm_103a next to this file (atomic rename).  `out` and `defines`
+    (preprocessor macros, e.g. FPSSFT_PHASE_TIMERS) build a variant under another name."""
+    if not force and not needs_build(out):
+        return out
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    cmd = [_nvcc(), *NVCC_FLAGS, "-I", os.path.join(_ROOT, "include"), "-o", tmp, *SOURCES]
+    cmd = [_nvcc(), *NVCC_FLAGS, *(f"-D{d}" for d in defines), "-I", os.path.join(_ROOT, "include"), "-o", tmp,
+           *SOURCES]
     try:
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
         if verbose:
             print(r.stdout + r.stderr)
-        os.replace(tmp, LIB_PATH)
+        os.replace(tmp, out)
     finally:
         if os.path.exists(tmp):
             os.unlink(tmp)
-    return LIB_PATH
+    return out
 
 
 class PlanInfo(ctypes.Structure):
@@ -103,10 +107,21 @@ SIGNATURES = {
     "fpssft_adjoint": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
     "fpssft_probe_gather": (_I, [_P, ctypes.c_int64, _I, _I, _I, _I, _P, _P]),
     "fpssft_l2_fetch_granularity": (_I, [_I, ctypes.POINTER(ctypes.c_int)]),
+    "fpssft_phase_read": (_I, [_P]),
     "fpssft_recover_noalloc": (_I, [_I, _I, _P, ctypes.POINTER(CParams), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fpssft_last_error": (ctypes.c_char_p, []),
     "fpssft_version": (ctypes.c_char_p, []),
 }
+
+
+def use_library(path):
+    """Load `path`, an in-tree build variant of the same sources (the phase-timer build), in place of
+    libfpssft.so.  Only before the first load() of the process."""
+    global _variant
+    with _lock:
+        if _lib is not None:
+            raise RuntimeError("the CUDA library is already loaded in this process")
+        _variant = path
 
 
 def load(auto_build=True):
@@ -115,11 +130,12 @@ def load(auto_build=True):
     with _lock:
         if _lib is not None:
             return _lib
-        if auto_build and needs_build():
+        path = _variant or LIB_PATH
+        if _variant is None and auto_build and needs_build():
             build()
-        if not os.path.exists(LIB_PATH):
-            raise FpssftError(ERR_UNSUPPORTED, f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
-        lib = ctypes.CDLL(LIB_PATH)
+        if not os.path.exists(path):
+            raise FpssftError(ERR_UNSUPPORTED, f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)
             fn.restype = res

@@ -993,6 +993,24 @@ extern "C" const char* fpssft_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* fpssft_version(void) { return "fpssft-gb300 0.1 (sm_103a)"; }
 
+static_assert(kNumPhases == FPSSFT_PHASE_COUNT && kPhaseWords == FPSSFT_PHASE_WORDS, "phase counter layout");
+
+extern "C" fpssft_status fpssft_phase_read(int64_t* out) {
+#ifdef FPSSFT_PHASE_TIMERS
+  if (!out) return fail(FPSSFT_ERR_INVALID, "null output");
+  unsigned long long h[kPhaseWords];
+  const unsigned long long z[kPhaseWords] = {};
+  FPSSFT_CUDA_TRY(cudaDeviceSynchronize());
+  FPSSFT_CUDA_TRY(cudaMemcpyFromSymbol(h, g_phase, sizeof(h)));
+  FPSSFT_CUDA_TRY(cudaMemcpyToSymbol(g_phase, z, sizeof(z)));
+  for (int i = 0; i < kPhaseWords; ++i) out[i] = (int64_t)h[i];
+  return FPSSFT_OK;
+#else
+  (void)out;
+  return fail(FPSSFT_ERR_UNSUPPORTED, "library built without FPSSFT_PHASE_TIMERS");
+#endif
+}
+
 // ================================================================================================
 // Recovery without any device allocation
 // ================================================================================================

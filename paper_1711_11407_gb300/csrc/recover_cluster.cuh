@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   __shared__ unsigned char* s_base[kMaxD + 1];  // each rank's dynamic shared memory (generic address)
 
   const int rank = (int)cluster.block_rank();
+  FPSSFT_PH_START();
   const int b = A.tab.order[blockIdx.x / (D + 1)];
   const int si = A.tab.sig_shape[b];
   const bool pf = A.prefetch != 0;
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   const int T = stop ? 0 : A.tab.sig_T[b];
   const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
   const int* sched_t = A.tau + (size_t)b * A.sched_stride;
+  FPSSFT_PH(kPhSetup);
   if (pf && T > 0) gather_one_line<D, 0, true>(bufA, x, sh, sched_a, sched_t, rank);
   int iters = 0;
   for (int t = 0; t < T; ++t) {
@@ -297,9 +299,13 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
       gather_one_line<D, 0, false>(bufA, x, sh, al, ta, rank);
     }
     __syncthreads();
+    FPSSFT_PH(kPhGather);
     float2* bins = fft_line(cur, bufB, sh, tws, stws, 1.0f / (float)L);
+    FPSSFT_PH(kPhFft);
     peel_line_keys<D, GS>(bins, sh, la, lkey, n_set, s_ca, s_ct, tws, rank);
+    FPSSFT_PH(kPhPeel);
     cluster.sync();   // every line peeled
+    FPSSFT_PH(kPhExchange);
 
     const size_t boff = reinterpret_cast<unsigned char*>(bins) - smem;
     int my_t0 = 0;
@@ -334,15 +340,22 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     }
     if (my_t0) atomicAdd(c_t0 + par, my_t0);
     if (my_ovf) atomicOr(c_ovf, 1);
+    FPSSFT_PH(kPhDecode);
     cluster.sync();   // every insert landed in every replica
+    FPSSFT_PH(kPhExchange);
     n_set = min(GS ? __ldcg(g_count) : *c_count, A.k_cap);
     iters = t + 1;
     if ((A.early_stop && c_t0[par] == 0) || *c_ovf != 0) break;   // the same verdict on every rank
   }
   if (pf) cp_async_wait<0>();
   cluster.sync();   // no rank reads another's shared memory past this point
+  FPSSFT_PH(kPhExchange);
+  FPSSFT_PH_ITERS(iters);
 
-  if (rank != 0) return;
+  if (rank != 0) {
+    FPSSFT_PH_FLUSH();
+    return;
+  }
   // output order: a bitmap of the grid points in the shared memory the set does not use (all of it
   // with GS), else sorted (key, position) pairs
   {
@@ -365,6 +378,8 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
         A.out_iters[b] = iters;
         A.out_status[b] = s_ovf ? kStatusCapacity : 0;
       }
+      FPSSFT_PH(kPhOutput);
+      FPSSFT_PH_FLUSH();
       return;
     }
   }
@@ -388,4 +403,6 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     A.out_iters[b] = iters;
     A.out_status[b] = s_ovf ? kStatusCapacity : 0;
   }
+  FPSSFT_PH(kPhOutput);
+  FPSSFT_PH_FLUSH();
 }

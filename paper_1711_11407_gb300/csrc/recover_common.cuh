@@ -7,6 +7,7 @@
 
 #include "fpssft.h"
 #include "fpssft_device.cuh"
+#include "phase_timers.cuh"
 
 using namespace fpssft;
 

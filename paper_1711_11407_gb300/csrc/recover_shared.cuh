@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
   set.k_cap = A.k_cap;
   set.hash_bits = A.hash_bits;
   const int hash_cap = 1 << A.hash_bits;
+  FPSSFT_PH_START();
 
   int loaded = -1;
   for (;;) {
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
     const int T = A.tab.sig_T[b];
     const int* sched_a = A.alpha + (size_t)b * A.sched_stride;
     const int* sched_t = A.tau + (size_t)b * A.sched_stride;
+    FPSSFT_PH(kPhSetup);
     if (pf && T > 0) gather_lines_async<D>(bufA, x, sh, sched_a, sched_t);
     int iters = 0;
     for (int t = 0; t < T; ++t) {
@@ -111,18 +113,23 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
         gather_lines<D, 0>(bufA, x, sh, al, ta);
       }
       __syncthreads();
+      FPSSFT_PH(kPhGather);
       if (threadIdx.x == 0) s_t0 = 0;
       float2* bins = fft_lines(cur, bufB, D + 1, sh, tw, 1.0f / (float)L, stw);
+      FPSSFT_PH(kPhFft);
       peel_set<D>(bins, sh, set, min(s_count, A.k_cap), s_ca, s_ct, tw);
       __syncthreads();
+      FPSSFT_PH(kPhPeel);
       decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf);
       __syncthreads();
+      FPSSFT_PH(kPhDecode);
       iters = t + 1;
       const bool stop = (A.early_stop && s_t0 == 0) || s_ovf != 0;
       if (stop) break;
     }
 
     if (pf) cp_async_wait<0>();   // a prefetch past the last iteration still lands before reuse
+    FPSSFT_PH_ITERS(iters);
     // output: keep |a| > theta0, in order of linear index (hash arrays reused as sort buffers)
     const int count = min(s_count, A.k_cap);
     auto key_of = [&](int i) { return set.lkey[i]; };
@@ -139,5 +146,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
       A.out_status[b] = s_ovf ? kStatusCapacity : 0;
     }
     __syncthreads();
+    FPSSFT_PH(kPhOutput);
   }
+  FPSSFT_PH_FLUSH();
 }

@@ -137,6 +137,7 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
   float2* my_stg = stg + warp * L;
   bool have_next = false;      // samples of the current iteration already requested
   bool likely_done = false;    // every T0 bin of the previous iteration was accepted
+  FPSSFT_PH(kPhSetup);
   if (T > 0) {
     int alr[D], tar[D];
     sched_row<D>(sh, sched_a, sched_t, alr, tar);
@@ -169,7 +170,9 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
 #pragma unroll
       for (int i = 0; i < R; ++i) v[i] = nxt[STAGED ? 0 : i];
     }
+    FPSSFT_PH(kPhGather);
     fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
+    FPSSFT_PH(kPhFft);
     have_next = t + 1 < T && !likely_done;
     if (have_next) {
       int alr[D], tar[D];
@@ -180,14 +183,17 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
         gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
     }
     __syncthreads();
+    FPSSFT_PH(kPhGather);
     if (threadIdx.x == 0) {
       *s_t0 = 0;
       *s_acc = 0;
     }
     peel_set_w<D>(bins, sh, set, min(*set.count, A.k_cap), s_ca, s_ct, tws);
     __syncthreads();
+    FPSSFT_PH(kPhPeel);
     decode_bins_w<D>(bins, sh, set, s_ca, s_ct, tws, A.th, s_t0, s_ovf, s_acc);
     __syncthreads();
+    FPSSFT_PH(kPhDecode);
     iters = t + 1;
     const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
     if (stop) break;
@@ -226,6 +232,7 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
   set.k_cap = A.k_cap;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  FPSSFT_PH_START();
 
   int loaded = -1;
   for (;;) {
@@ -276,6 +283,7 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
       case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
       default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
     }
+    FPSSFT_PH_ITERS(iters);
 
     const int count = min(s_count, A.k_cap);
     int* tkey = reinterpret_cast<int*>(bins);                        // the bins are free now
@@ -299,5 +307,7 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
       A.out_status[b] = s_ovf ? kStatusCapacity : 0;
     }
     __syncthreads();
+    FPSSFT_PH(kPhOutput);
   }
+  FPSSFT_PH_FLUSH();
 }

@@ -68,3 +68,10 @@ def test_null_plan_rejected():
     assert lib.fpssft_project(None, None, None, None, None, 1, None, None) == _lib.ERR_INVALID
     assert lib.fpssft_adjoint(None, 0, None, None, None, None, 1, None, None, None, None) == _lib.ERR_INVALID
     assert b"null plan" in lib.fpssft_last_error()
+
+
+def test_phase_read_is_unsupported_in_the_default_build():
+    lib = _lib.load()
+    buf = (ctypes.c_int64 * 11)()
+    assert lib.fpssft_phase_read(buf) == _lib.ERR_UNSUPPORTED
+    assert b"FPSSFT_PHASE_TIMERS" in lib.fpssft_last_error()
