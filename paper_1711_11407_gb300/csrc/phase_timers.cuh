@@ -10,7 +10,8 @@
 // counters, the iterations it ran, its total cycles and the global-timer nanoseconds of the same
 // span (their ratio converts cycles to time at the clock the launch actually ran at);
 // fpssft_phase_read copies g_phase out and clears it.  In the register path the wait for samples
-// prefetched into registers is charged to the FFT, where the registers are first read.
+// prefetched into registers falls where they are first read: the copy into the FFT's inputs (the
+// gather phase), or the FFT itself where the compiler folds that copy away.
 #pragma once
 
 // Phase indices; the order is the one of FPSSFT_PHASE_COUNT's documentation in fpssft.h.
