@@ -17,7 +17,7 @@ from __future__ import annotations
 import json
 import math
 import os
-from dataclasses import asdict, replace
+from dataclasses import replace
 
 import numpy as np
 import torch

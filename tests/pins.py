@@ -7,7 +7,6 @@ Nothing here calls the CUDA library.
 """
 from __future__ import annotations
 
-import itertools
 import math
 import os
 from fractions import Fraction

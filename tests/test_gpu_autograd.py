@@ -2,7 +2,6 @@
 
 The GPU computes in FP32; its gradients are compared with finite differences of the oracle's FP64
 forward maps and with the oracle's explicit dense adjoints, on small cubes (8x8x8 and 2-D)."""
-import math
 
 import numpy as np
 import pytest
