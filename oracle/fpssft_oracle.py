@@ -262,6 +262,24 @@ def linear_index(k, dims):
     return lin
 
 
+def merge(S, cands, k_cap):
+    """Merge one iteration's decoded (m, k, a) candidates into the recovered set S (dict k -> a).
+
+    Sec. 2.2 adds each decoded frequency to the recovered set and is silent on a frequency that is
+    already there; reading A9: its amplitude accumulates the decoded value, which is the residual
+    left after that frequency's current amplitude was peeled.  A new frequency is dropped when S
+    already holds k_cap entries.  Returns False when one was dropped."""
+    ok = True
+    for _, kk, aa in cands:
+        if kk in S:
+            S[kk] = S[kk] + aa
+        elif len(S) < k_cap:
+            S[kk] = aa
+        else:
+            ok = False
+    return ok
+
+
 def recover(x, alpha, tau, p, init=None, T=None, keep_history=False):
     """Run the FPS-SFT iterations on one cube x (complex, shape dims) with schedule alpha[t], tau[t].
 
@@ -291,13 +309,8 @@ def recover(x, alpha, tau, p, init=None, T=None, keep_history=False):
         if p.early_stop and n_t0 == 0:
             hist.append((len(S), n_t0))
             break
-        for _, kk, aa in cands:
-            if kk in S:
-                S[kk] = S[kk] + aa
-            elif len(S) < p.k_cap:
-                S[kk] = aa
-            else:
-                status = STATUS_CAPACITY
+        if not merge(S, cands, p.k_cap):
+            status = STATUS_CAPACITY
         hist.append((len(S), n_t0))
         if status != STATUS_OK:
             break

@@ -191,6 +191,24 @@ def check_tiny_support(O):
     del rng
 
 
+# --- a re-decoded frequency accumulates its residual (reading A9) ---------------------------------
+
+def check_redecode_accumulates(O):
+    """Resume from the planted support with every amplitude off by delta: peeling leaves -delta
+    alone in each occupied bin, which decodes to the same frequency, so accumulating brings every
+    amplitude back to the planted one (to rounding) and the next iteration finds nothing.  Keeping
+    the old amplitude, or replacing it by the decoded value, leaves delta or -delta instead."""
+    dims = (16, 24)
+    for seed in (6, 7):
+        k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence(seed), dims, 10, 8)
+        delta = 0.1 * np.exp(2j * np.pi * np.random.default_rng(seed).random(len(a)))
+        r = O.recover(x, al, ta, O.Params(T=8, k_cap=64), init=(k, a + delta))
+        order = np.argsort(O.linear_index(k, dims))
+        assert r.status == 0 and np.array_equal(r.k, k[order]), "the support must stay the planted one"
+        assert np.allclose(r.a, a[order], atol=1e-12), "re-decoded amplitudes must accumulate to the planted ones"
+        assert r.iters >= 2, "the first iteration must find the residuals"
+
+
 # --- construction-subtraction: bins-domain equals the literal order -------------------------------
 
 def check_peel_equivalence(O):

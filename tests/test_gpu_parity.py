@@ -625,3 +625,42 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
             k, a = out.signal(b)
             assert_same_set(k, a, ref, f"dims {dims} K {K} path {path} gather {gm} k_cap {kcap} signal {b}")
             assert int(out.iters[b]) == ref.iters and int(out.status[b]) == ref.status
+
+
+@pytest.mark.parametrize("fft_path,k_cap", [(1, 64), (2, 64), (3, 64), (3, 16000)])
+def test_redecoded_frequencies_accumulate_their_residual_like_the_oracle(fft_path, k_cap):
+    """Reading A9 on every kernel path (and the cluster path's set in global workspace): resumed
+    from the planted support with every amplitude off by delta, the next iteration decodes each
+    residual -delta at the same frequency and adds it, giving the oracle's set, which is the planted
+    spectrum; keeping or replacing the old amplitude would leave delta or -delta."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = small_batch([(32, 64)], 3, K=lambda N: 12, T=8, seed=11)    # L = 64: every path applies
+    p = configs.params_for(wl, T=8, k_cap=k_cap, fft_path=fft_path)
+    plan = Plan(wl.dims, p)
+    assert plan.info["fft_path"] == fft_path
+    cubes, offs, al, ta = to_dev(wl)
+    rng = np.random.default_rng(11)
+    kk = np.zeros((wl.batch, plan.k_cap, 2), np.int32)
+    aa = np.zeros((wl.batch, plan.k_cap), np.complex64)
+    counts = np.zeros(wl.batch, np.int32)
+    inits = []
+    for b in range(wl.batch):
+        k = np.asarray(wl.k_true[b], np.int64)
+        a0 = (np.asarray(wl.a_true[b]) + 0.1 * np.exp(2j * np.pi * rng.random(len(k)))).astype(np.complex64)
+        kk[b, :len(k)] = k
+        aa[b, :len(k)] = a0
+        counts[b] = len(k)
+        inits.append((k, a0.astype(np.complex128)))
+    out = plan.alloc_output()
+    out.k.copy_(torch.from_numpy(kk))
+    out.a.copy_(torch.from_numpy(aa))
+    plan.recover(cubes, offs, al, ta, out=out, init_count=torch.from_numpy(counts).to(dev()))
+    torch.cuda.synchronize()
+    for b in range(wl.batch):
+        ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, 8), init=inits[b])
+        k, a = out.signal(b)
+        assert_same_set(k, a, ref, f"path {fft_path} k_cap {k_cap} signal {b}")
+        assert int(out.iters[b]) == ref.iters >= 2 and int(out.status[b]) == 0
+        order = np.argsort(O.linear_index(np.asarray(wl.k_true[b], np.int64), tuple(int(v) for v in wl.dims[b])))
+        assert np.allclose(ref.a, np.asarray(wl.a_true[b])[order], atol=1e-5)
+    plan.close()

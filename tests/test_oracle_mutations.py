@@ -24,6 +24,7 @@ CHECKS = [
     pins.check_adjoints,
     pins.check_deadlock,
     pins.check_fig3_samples,
+    pins.check_redecode_accumulates,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -105,6 +106,30 @@ def _synth_line0_only(k, a, alpha, tau, dims):
     return out
 
 
+def _merge_overwrites(S, cands, k_cap):
+    # a re-decoded frequency takes the decoded residual as its amplitude
+    ok = True
+    for _, kk, aa in cands:
+        if kk in S or len(S) < k_cap:
+            S[kk] = aa
+        else:
+            ok = False
+    return ok
+
+
+def _merge_ignores_known(S, cands, k_cap):
+    # a frequency already in the set keeps its amplitude
+    ok = True
+    for _, kk, aa in cands:
+        if kk in S:
+            continue
+        if len(S) < k_cap:
+            S[kk] = aa
+        else:
+            ok = False
+    return ok
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -119,6 +144,8 @@ MUTATIONS = {
     "adjoint uses the forward DFT": ("project_adjoint", _adjoint_forward_dft),
     "decode uses the inverted ratio": ("classify_decode", _classify_inverted_ratio),
     "synthesis ignores the offset lines": ("synth", _synth_line0_only),
+    "re-decoded amplitude overwrites": ("merge", _merge_overwrites),
+    "re-decoded frequency ignored": ("merge", _merge_ignores_known),
 }
 
 

@@ -84,6 +84,10 @@ def test_resume_from_complete_set_stops_after_one_iteration():
     assert np.allclose(r.a, a[np.argsort(O.linear_index(k, (16, 24)))], atol=1e-12)
 
 
+def test_redecoded_frequency_accumulates_its_residual():
+    pins.check_redecode_accumulates(O)
+
+
 def test_two_sparse_bin_with_unequal_magnitudes_is_rejected():
     # two frequencies on the same bin of a row (slope (0,1)) with different column index:
     # line 1 (tau + e_0) rotates them differently, so |s_1| != |s_0| and T1 rejects the bin
