@@ -191,6 +191,13 @@ def peel_literal(samples, k, a, alpha, tau, dims):
 # 1-sparsity test and OFDM-trick decode: Sec. 2.1, Sec. 2.2, Eq. decoding
 # ---------------------------------------------------------------------------------------------
 
+def projects_to(m, k, alpha, dims):
+    """T3: the decoded frequency k lies on bin m of the line with slope alpha (Eq. orthogonality).
+    A bin that passed T0-T2 by accident (several frequencies) decodes to a k that lands on another
+    bin with probability 1 - 1/L."""
+    return int(bin_index(np.asarray(k), alpha, dims)) == int(m)
+
+
 def classify_decode(bins, alpha, tau, dims, p):
     """Decode every bin that passes the 1-sparsity tests.
 
@@ -230,7 +237,7 @@ def classify_decode(bins, alpha, tau, dims, p):
             k.append(r % dims[d])
         if not ok:
             continue
-        if int(bin_index(np.asarray(k), alpha, dims)) != int(m):
+        if not projects_to(m, k, alpha, dims):
             continue
         a = s0[m] * np.conj(line_phase(np.asarray(k), tau, dims, 0))
         if p.amp_average:

@@ -174,6 +174,29 @@ def check_single_sinusoid(O):
                     assert abs(aa - a) < 1e-12 * max(1.0, abs(a)), "decoded amplitude differs from planted"
 
 
+# --- T3: a bin whose decoded frequency maps to another bin is rejected (Eq. orthogonality) --------
+
+def check_projection_test(O):
+    """Bins made by hand on an 8 x 8 grid (L = 8, c = (1, 1)), slope (1, 3), offset (3, 5): line 0
+    holds a e^{j 2 pi (k_0 tau_0 + k_1 tau_1) / 8} and line d+1 that times e^{j 2 pi k_d / 8}
+    (Eq. freqSum), for k = (1, 1), whose bin is [1 + 3]_8 = 4.  Placed in bin 4 the values decode to
+    k and a; placed in bin 0 they pass T0-T2 alike but must be rejected."""
+    dims, alpha, tau, k, a = (8, 8), (1, 3), (3, 5), (1, 1), 0.8 * np.exp(0.7j)
+    s0 = a * np.exp(2j * np.pi * (k[0] * tau[0] + k[1] * tau[1]) / 8)
+    vals = [s0, s0 * np.exp(2j * np.pi * k[0] / 8), s0 * np.exp(2j * np.pi * k[1] / 8)]
+    p = O.Params(T=1, k_cap=4)
+    for m, accept in ((4, True), (0, False)):
+        bins = np.zeros((3, 8), np.complex128)
+        bins[:, m] = vals
+        cands, n0 = O.classify_decode(bins, alpha, tau, dims, p)
+        assert n0 == 1, "one non-zero bin"
+        if accept:
+            assert len(cands) == 1 and cands[0][0] == 4 and cands[0][1] == k, "the consistent bin must decode to k"
+            assert abs(cands[0][2] - a) < 1e-12, "amplitude of Eq. decoding"
+        else:
+            assert cands == [], "a bin whose decoded k lies on another bin must be rejected (T3)"
+
+
 # --- exact recovery on tiny cubes equals the dense DFT's support ----------------------------------
 
 def check_tiny_support(O):

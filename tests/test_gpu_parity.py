@@ -664,3 +664,34 @@ def test_redecoded_frequencies_accumulate_their_residual_like_the_oracle(fft_pat
         order = np.argsort(O.linear_index(np.asarray(wl.k_true[b], np.int64), tuple(int(v) for v in wl.dims[b])))
         assert np.allclose(ref.a, np.asarray(wl.a_true[b])[order], atol=1e-5)
     plan.close()
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_decode_rejects_a_bin_that_decodes_off_its_bin(fp64):
+    """T3 on the GPU with bins made by hand (the oracle pin's case): the values of k = (1, 1) on an
+    8 x 8 grid with slope (1, 3) and offset (3, 5) decode to k and a in k's own bin 4, and the same
+    values placed in bin 0 pass T0-T2 but are rejected; FP32-certified and FP64 decisions alike."""
+    from paper_1711_11407_gb300.api import Params, Plan
+    dims, alpha, tau, k, a = (8, 8), (1, 3), (3, 5), (1, 1), 0.8 * np.exp(0.7j)
+    s0 = a * np.exp(2j * np.pi * (k[0] * tau[0] + k[1] * tau[1]) / 8)
+    vals = np.asarray([s0, s0 * np.exp(2j * np.pi * k[0] / 8), s0 * np.exp(2j * np.pi * k[1] / 8)])
+    plan = Plan(np.asarray([dims, dims], np.int64), Params(T=1, k_cap=8, fp64_decisions=fp64))
+    bins = np.zeros((2, 1, 3, plan.L_max), np.complex64)
+    bins[0, 0, :, 4] = vals
+    bins[1, 0, :, 0] = vals
+    d = dev()
+    al = torch.tensor([[alpha], [alpha]], dtype=torch.int32, device=d)
+    ta = torch.tensor([[tau], [tau]], dtype=torch.int32, device=d)
+    kk = torch.zeros((2, plan.k_cap, 2), dtype=torch.int32, device=d)
+    aa = torch.zeros((2, plan.k_cap), dtype=torch.complex64, device=d)
+    count = torch.zeros(2, dtype=torch.int32, device=d)
+    t0 = torch.zeros(2, dtype=torch.int32, device=d)
+    status = torch.zeros(2, dtype=torch.int32, device=d)
+    plan.decode(torch.from_numpy(bins).to(d), al, ta, kk, aa, count, t0, status)
+    torch.cuda.synchronize()
+    assert t0.tolist() == [1, 1] and status.tolist() == [0, 0]
+    assert count.tolist() == [1, 0], "the bin whose decoded k lies on another bin must be rejected (T3)"
+    assert tuple(kk[0, 0].tolist()) == k and abs(complex(aa[0, 0].item()) - a) < 1e-5
+    ref, n0 = O.classify_decode(bins[0, 0].astype(np.complex128), alpha, tau, dims, O.Params(T=1, k_cap=8))
+    assert n0 == 1 and len(ref) == 1 and ref[0][1] == k
+    plan.close()

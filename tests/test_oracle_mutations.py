@@ -25,6 +25,7 @@ CHECKS = [
     pins.check_deadlock,
     pins.check_fig3_samples,
     pins.check_redecode_accumulates,
+    pins.check_projection_test,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -130,6 +131,10 @@ def _merge_ignores_known(S, cands, k_cap):
     return ok
 
 
+def _projection_test_dropped(m, k, alpha, dims):
+    return True
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -146,6 +151,7 @@ MUTATIONS = {
     "synthesis ignores the offset lines": ("synth", _synth_line0_only),
     "re-decoded amplitude overwrites": ("merge", _merge_overwrites),
     "re-decoded frequency ignored": ("merge", _merge_ignores_known),
+    "projection test T3 dropped": ("projects_to", _projection_test_dropped),
 }
 
 

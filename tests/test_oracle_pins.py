@@ -84,6 +84,10 @@ def test_resume_from_complete_set_stops_after_one_iteration():
     assert np.allclose(r.a, a[np.argsort(O.linear_index(k, (16, 24)))], atol=1e-12)
 
 
+def test_projection_test_rejects_a_bin_that_decodes_off_its_bin():
+    pins.check_projection_test(O)
+
+
 def test_redecoded_frequency_accumulates_its_residual():
     pins.check_redecode_accumulates(O)
 
