@@ -197,6 +197,39 @@ def check_projection_test(O):
             assert cands == [], "a bin whose decoded k lies on another bin must be rejected (T3)"
 
 
+# --- T1 and T2 on either side of their tolerances (Sec. 2.1 magnitudes, Eq. decoding grid) --------
+
+def sparsity_test_bins():
+    """Hand-made bins of k = (1, 1) in its own bin 4 (8 x 8, slope (1, 3), offset (3, 5)), each case
+    with one line perturbed: (name, bins [3][8], accepted under rho = 1e-3, eta = 0.05)."""
+    k, tau, a = (1, 1), (3, 5), 0.8 * np.exp(0.7j)
+    s0 = a * np.exp(2j * np.pi * (k[0] * tau[0] + k[1] * tau[1]) / 8)
+    cases = []
+    for name, phase_off, mag, accept in (("phase 0.3 of a grid step off", 0.3, 1.0, False),
+                                         ("phase 0.02 of a grid step off", 0.02, 1.0, True),
+                                         ("magnitude 1 % off", 0.0, 1.01, False),
+                                         ("magnitude 0.05 % off", 0.0, 1.0005, True)):
+        bins = np.zeros((3, 8), np.complex128)
+        bins[0, 4] = s0
+        bins[1, 4] = s0 * np.exp(2j * np.pi * (k[0] + phase_off) / 8)
+        bins[2, 4] = s0 * mag * np.exp(2j * np.pi * k[1] / 8)
+        cases.append((name, bins, accept))
+    return cases
+
+
+def check_sparsity_tests(O):
+    """A phase more than eta of a grid step from the grid (T2), or a line magnitude more than rho
+    from line 0's (T1), rejects the bin; within the tolerances the bin decodes to k = (1, 1)."""
+    p = O.Params(T=1, k_cap=4, theta0=1e-3, rho=1e-3, eta=0.05)
+    for name, bins, accept in sparsity_test_bins():
+        cands, n0 = O.classify_decode(bins, (1, 3), (3, 5), (8, 8), p)
+        assert n0 == 1, name
+        if accept:
+            assert len(cands) == 1 and cands[0][1] == (1, 1), f"{name}: must decode to (1, 1)"
+        else:
+            assert cands == [], f"{name}: must be rejected"
+
+
 # --- exact recovery on tiny cubes equals the dense DFT's support ----------------------------------
 
 def check_tiny_support(O):

@@ -695,3 +695,36 @@ def test_decode_rejects_a_bin_that_decodes_off_its_bin(fp64):
     ref, n0 = O.classify_decode(bins[0, 0].astype(np.complex128), alpha, tau, dims, O.Params(T=1, k_cap=8))
     assert n0 == 1 and len(ref) == 1 and ref[0][1] == k
     plan.close()
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_decode_applies_magnitude_and_grid_tolerances_like_the_oracle(fp64):
+    """T1 and T2 on the GPU with the oracle pin's hand-made bins: a line phase 0.3 of a grid step
+    off (eta = 0.05) or a line magnitude 1 % off (rho = 1e-3) rejects the bin, 0.02 of a step or
+    0.05 % decodes it; one signal per case, FP32-certified and FP64 decisions alike."""
+    import pins
+    from paper_1711_11407_gb300.api import Params, Plan
+    cases = pins.sparsity_test_bins()
+    B = len(cases)
+    plan = Plan(np.asarray([(8, 8)] * B, np.int64), Params(T=1, k_cap=8, fp64_decisions=fp64))
+    bins = np.zeros((B, 1, 3, plan.L_max), np.complex64)
+    for b, (_, bb, _) in enumerate(cases):
+        bins[b, 0, :, :8] = bb
+    d = dev()
+    al = torch.tensor([[(1, 3)]] * B, dtype=torch.int32, device=d)
+    ta = torch.tensor([[(3, 5)]] * B, dtype=torch.int32, device=d)
+    kk = torch.zeros((B, plan.k_cap, 2), dtype=torch.int32, device=d)
+    aa = torch.zeros((B, plan.k_cap), dtype=torch.complex64, device=d)
+    count = torch.zeros(B, dtype=torch.int32, device=d)
+    t0 = torch.zeros(B, dtype=torch.int32, device=d)
+    status = torch.zeros(B, dtype=torch.int32, device=d)
+    plan.decode(torch.from_numpy(bins).to(d), al, ta, kk, aa, count, t0, status)
+    torch.cuda.synchronize()
+    p = O.Params(T=1, k_cap=8, theta0=1e-3, rho=1e-3, eta=0.05)
+    for b, (name, _, accept) in enumerate(cases):
+        ref, n0 = O.classify_decode(bins[b, 0, :, :8].astype(np.complex128), (1, 3), (3, 5), (8, 8), p)
+        assert int(t0[b]) == n0 == 1 and int(status[b]) == 0, name
+        assert int(count[b]) == len(ref) == (1 if accept else 0), name
+        if accept:
+            assert tuple(kk[b, 0].tolist()) == ref[0][1] == (1, 1), name
+    plan.close()

@@ -2,6 +2,7 @@
 
 A pin set that cannot tell a dropped term, a wrong sign, a wrong index or a transposed operand
 from the correct oracle would not pin it; these tests show that it can."""
+import dataclasses
 import math
 
 import numpy as np
@@ -26,6 +27,7 @@ CHECKS = [
     pins.check_fig3_samples,
     pins.check_redecode_accumulates,
     pins.check_projection_test,
+    pins.check_sparsity_tests,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -135,6 +137,12 @@ def _projection_test_dropped(m, k, alpha, dims):
     return True
 
 
+def _classify_without(field):
+    def classify(bins, alpha, tau, dims, p):
+        return _orig["classify_decode"](bins, alpha, tau, dims, dataclasses.replace(p, **{field: 1e9}))
+    return classify
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -152,6 +160,8 @@ MUTATIONS = {
     "re-decoded amplitude overwrites": ("merge", _merge_overwrites),
     "re-decoded frequency ignored": ("merge", _merge_ignores_known),
     "projection test T3 dropped": ("projects_to", _projection_test_dropped),
+    "magnitude test T1 dropped": ("classify_decode", _classify_without("rho")),
+    "grid test T2 dropped": ("classify_decode", _classify_without("eta")),
 }
 
 

@@ -88,6 +88,10 @@ def test_projection_test_rejects_a_bin_that_decodes_off_its_bin():
     pins.check_projection_test(O)
 
 
+def test_magnitude_and_grid_tests_on_either_side_of_their_tolerances():
+    pins.check_sparsity_tests(O)
+
+
 def test_redecoded_frequency_accumulates_its_residual():
     pins.check_redecode_accumulates(O)
 
