@@ -17,7 +17,9 @@
  *   - Complex numbers are complex64: two floats (re, im), interleaved.
  *   - A batch holds `batch` cubes with per-signal shapes dims[b][0..D-1] (1 <= D <= 4).  Cubes are
  *     C-order (last dimension fastest) and concatenated in one device buffer; offsets[b] (int64,
- *     device) is the element offset of cube b.
+ *     device) is the element offset of cube b, which occupies elements [offsets[b], offsets[b] +
+ *     N_b) of that buffer.  The library cannot see the buffer's size: offsets outside it are the
+ *     caller's error (the Python binding checks them against the tensor before every call).
  *   - L_b = LCM of signal b's dims; L_max = max_b L_b.  Bin and line arrays are
  *     [batch][n_sched][D+1][L_max] complex64; entries m >= L_b of a line are written as zero.
  *   - Schedules alpha, tau are int32 [batch][n_sched][D] (device) with 0 <= alpha_d, tau_d < N_d.
