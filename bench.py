@@ -64,6 +64,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest rank's time is the job's); x itself when alone."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: what every rank processed in a step over the slowest rank's step time."""
+    return units_per_rank * world / (ms_per_step / 1000.0)
+
+
 def stratified(wl, n, seed=0):
     """n signal indices spread evenly over the distinct shapes of the workload."""
     rng = np.random.default_rng(seed)
@@ -397,13 +413,9 @@ def main():
         if world > 1:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = wl.batch * world / (ms_per_step / 1000.0)
+    value = job_rate(wl.batch, world, ms_per_step)
 
     # ---- correctness of what was timed: exact support vs the planted spectra ---------------------
     torch.cuda.synchronize()
@@ -515,22 +527,16 @@ def main():
                 a1.synchronize()
                 map_ms.append(a0.elapsed_time(a1))
         mapped_same = bool(torch.equal(h_out.count, out.count.cpu()))
-        te = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_step = float(te.item()) / args.steps
+        e2e_step = max_over_ranks(sum(e2e_ms), world, dev) / args.steps
         same = bool(torch.equal(h_out.count, out.count.cpu()))
         h2d = sum(int(x.numel() * x.element_size()) for x in (h_cubes, h_offs, h_alpha, h_tau))
         d2h = sum(int(getattr(h_out, f).numel() * getattr(h_out, f).element_size()) for f in ("k", "a", "count", "iters", "status"))
-        line["e2e"] = {"value": wl.batch * world / (e2e_step / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        line["e2e"] = {"value": job_rate(wl.batch, world, e2e_step), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step, "call": "fpssft_recover_host",
                        "matches_device_run": same}
-        tm = torch.tensor([sum(map_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        map_step = float(tm.item()) / args.steps
+        map_step = max_over_ranks(sum(map_ms), world, dev) / args.steps
         small = sum(int(x.numel() * x.element_size()) for x in (h_offs, h_alpha, h_tau))
-        line["e2e_host_mapped"] = {"value": wl.batch * world / (map_step / 1000.0), "unit": UNIT,
+        line["e2e_host_mapped"] = {"value": job_rate(wl.batch, world, map_step), "unit": UNIT,
                                    "h2d_bytes_per_step": small, "d2h_bytes_per_step": d2h, "ms_per_step": map_step,
                                    "call": "fpssft_recover with the cubes in pinned host memory (read in place)",
                                    "cube_bytes_read_in_place_algorithmic": useful, "matches_device_run": mapped_same}

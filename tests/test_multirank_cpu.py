@@ -64,3 +64,39 @@ def test_two_gloo_ranks_shard_and_gather_equal_the_whole_batch():
         p.join(timeout=120)
     assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
     assert q.get(timeout=5) is True
+
+
+def _bench_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r's timed region took 10 * (r + 1) ms over 5 steps; every rank processed 4096 signals
+    total = bench.max_over_ranks(10.0 * (rank + 1), world, "cpu")
+    q.put((rank, total, bench.job_rate(4096, world, total / 5)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_benchmark_takes_the_slowest_rank_and_counts_every_rank_s_signals():
+    """The benchmark's cross-rank reduction on two gloo ranks: both ranks see the slowest rank's
+    time, and the job's rate counts the signals of both ranks over that time."""
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench
+    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, total, rate in got:
+        assert total == 20.0
+        assert abs(rate - 2 * 4096 / (4.0 / 1000.0)) < 1e-6
