@@ -58,3 +58,22 @@ def test_source_hash_ignores_comments_and_whitespace_but_not_code():
     assert bench.strip_comments('const char* s = "// kept"; // dropped') == 'const char* s = "// kept";'
     h = bench.source_hash()
     assert len(h) == 16 and h == bench.source_hash()
+
+
+def test_traffic_record_scales_by_signals_and_expires_with_the_kernel_code(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed DRAM record, scaled from its batch to the bench's,
+    only while the record's hash matches the kernel code (a comment-only edit keeps it)."""
+    csrc = tmp_path / "paper_1711_11407_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_text("__global__ void k() { }  // v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec = {"source_hash": bench.source_hash(), "batch": 1024, "dram_bytes_per_launch": 1000.0}
+    (tmp_path / "profiles" / "k_recover_wl.json").write_text(json.dumps(rec))
+    traffic, path = bench.profiled_traffic("wl", 4096)
+    assert traffic == 4000.0 and path.endswith("k_recover_wl.json")
+    (csrc / "k.cu").write_text("__global__ void k() { }  // v2, comment only\n")
+    assert bench.profiled_traffic("wl", 4096)[0] == 4000.0
+    (csrc / "k.cu").write_text("__global__ void k() { int x = 1; }\n")
+    assert bench.profiled_traffic("wl", 4096)[0] is None
+    assert bench.profiled_traffic("other", 4096) == (None, None)
