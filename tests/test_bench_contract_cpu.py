@@ -77,3 +77,25 @@ def test_traffic_record_scales_by_signals_and_expires_with_the_kernel_code(tmp_p
     (csrc / "k.cu").write_text("__global__ void k() { int x = 1; }\n")
     assert bench.profiled_traffic("wl", 4096)[0] is None
     assert bench.profiled_traffic("other", 4096) == (None, None)
+
+
+def test_clock_summary_keeps_this_gpu_inside_the_timed_region():
+    """The clocks record: only this GPU's samples that arrived inside the timed region count; the
+    median SM clock, the max clock and every throttle reason seen active are reported."""
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)
+    cs.uuid, cs.proc = "GPU-aaa", None
+
+    def row(uuid, sm, reasons=("Not Active",) * 4):
+        return ", ".join(["0", uuid, str(sm), "2070", "900.5", "0x0", *reasons]) + "\n"
+
+    cs.lines = [(0.5, row("GPU-aaa", 1000)),                                   # before the region
+                (1.1, row("GPU-aaa", 2070)),
+                (1.2, row("GPU-bbb", 500, ("Active",) * 4)),                  # another GPU
+                (1.3, row("GPU-aaa", 2040, ("Not Active", "Not Active", "Not Active", "Active"))),
+                (1.4, row("GPU-aaa", 2055)),
+                (9.0, row("GPU-aaa", 300, ("Active",) * 4))]                  # after the region
+    cs.t0, cs.t1 = 1.0, 1.5
+    s = cs.summary()
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs.t0, cs.t1 = 20.0, 21.0
+    assert cs.summary()["samples"] == 0
