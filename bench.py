@@ -443,6 +443,9 @@ def main():
                 "peak_source": f"{peak_src} (hbm_gbs, copy bandwidth; kernel timed alone: burst figure)",
                 "algorithmic_bytes_per_launch": useful,
                 "kernel": f"{kname} ({kdesc}; one launch per step, CUDA events on the launching stream)"}
+    if traffic is not None:      # DRAM bytes actually moved per second (sectors, not useful samples)
+        roofline["traffic_gbs"] = traffic / (ms_per_step / 1000.0) / 1e9
+        roofline["traffic_frac"] = roofline["traffic_gbs"] / float(peaks["hbm_gbs"])
     # second view: the gather against the measured random-access ceiling of this GPU.  Each line
     # position reads one adjacent pair (lines tau and tau + e_{D-1}) and D - 1 isolated samples.
     if not args.quick or args.ceiling:
