@@ -45,6 +45,13 @@ def check_line_dft_definition(O, Ls=(1, 5, 12, 30)):
         ref /= L
         got = O.line_dft(s)
         assert np.allclose(got, ref, atol=1e-12), f"line DFT differs from Eq. hs at L={L}"
+        # the inverse used by the literal peel: s(l) = sum_m s_hat(m) e^{+j 2 pi l m / L}, by brute force
+        inv = np.zeros((2, L), np.complex128)
+        for l in range(L):
+            for m in range(L):
+                inv[:, l] += ref[:, m] * complex(math.cos(2 * math.pi * l * m / L), math.sin(2 * math.pi * l * m / L))
+        assert np.allclose(O.line_idft(ref), inv, atol=1e-12), f"inverse line DFT differs at L={L}"
+        assert np.allclose(inv, s, atol=1e-12), f"the brute-force inverse must return the samples at L={L}"
 
 
 # --- projection-slice identity (Eq. lines + Eq. freqSum vs sampling + Eq. hs) ----------------------

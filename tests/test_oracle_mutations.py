@@ -143,6 +143,10 @@ def _classify_without(field):
     return classify
 
 
+def _idft_unscaled(s_hat):
+    return np.fft.ifft(s_hat, axis=-1)
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -162,6 +166,7 @@ MUTATIONS = {
     "projection test T3 dropped": ("projects_to", _projection_test_dropped),
     "magnitude test T1 dropped": ("classify_decode", _classify_without("rho")),
     "grid test T2 dropped": ("classify_decode", _classify_without("eta")),
+    "inverse line DFT loses the factor L": ("line_idft", _idft_unscaled),
 }
 
 
