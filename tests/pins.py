@@ -254,6 +254,24 @@ def check_tiny_support(O):
     del rng
 
 
+# --- the early stop (reading A11): the first iteration that finds no bin on line 0 is the last -------
+
+def check_early_stop(O):
+    """Resumed from the complete set, the first iteration peels every bin to zero and is the last;
+    from scratch, the run ends one iteration after the set became complete (that iteration finds
+    nothing), far below the budget."""
+    dims, T = (16, 24), 40
+    k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence(6), dims, 10, T)
+    p = O.Params(T=T, k_cap=64)
+    r = O.recover(x, al, ta, p, init=(k, a))
+    assert r.iters == 1, "a complete set must stop after one iteration"
+    full = O.recover(x, al, ta, p, keep_history=True)
+    sizes = [h[0] for h in full.history]
+    done = sizes.index(len(k)) + 1                  # iterations until the set was complete
+    assert full.iters == done + 1 < T, "the run must end one iteration after the set is complete"
+    assert full.history[-1][1] == 0, "the last iteration found no bin passing T0"
+
+
 # --- a re-decoded frequency accumulates its residual (reading A9) ---------------------------------
 
 def check_redecode_accumulates(O):

@@ -28,6 +28,7 @@ CHECKS = [
     pins.check_redecode_accumulates,
     pins.check_projection_test,
     pins.check_sparsity_tests,
+    pins.check_early_stop,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -147,6 +148,12 @@ def _idft_unscaled(s_hat):
     return np.fft.ifft(s_hat, axis=-1)
 
 
+def _classify_never_empty(bins, alpha, tau, dims, p):
+    # the early stop never fires: every iteration reports a bin passing T0
+    cands, n0 = _orig["classify_decode"](bins, alpha, tau, dims, p)
+    return cands, n0 + 1
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -167,6 +174,7 @@ MUTATIONS = {
     "magnitude test T1 dropped": ("classify_decode", _classify_without("rho")),
     "grid test T2 dropped": ("classify_decode", _classify_without("eta")),
     "inverse line DFT loses the factor L": ("line_idft", _idft_unscaled),
+    "early stop never fires": ("classify_decode", _classify_never_empty),
 }
 
 

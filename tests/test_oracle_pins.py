@@ -92,6 +92,10 @@ def test_magnitude_and_grid_tests_on_either_side_of_their_tolerances():
     pins.check_sparsity_tests(O)
 
 
+def test_early_stop_ends_the_run_one_iteration_after_the_set_is_complete():
+    pins.check_early_stop(O)
+
+
 def test_redecoded_frequency_accumulates_its_residual():
     pins.check_redecode_accumulates(O)
 
