@@ -75,3 +75,28 @@ def test_phase_read_is_unsupported_in_the_default_build():
     buf = (ctypes.c_int64 * 11)()
     assert lib.fpssft_phase_read(buf) == _lib.ERR_UNSUPPORTED
     assert b"FPSSFT_PHASE_TIMERS" in lib.fpssft_last_error()
+
+
+def test_every_call_rejects_a_null_plan_or_pointer_on_the_host():
+    """The error contract without a device: a null plan (or null params / buffer) is
+    FPSSFT_ERR_INVALID with a message, before any CUDA call; destroying a null plan is a no-op."""
+    lib = _lib.load()
+    Z = None
+    cases = {
+        "fpssft_plan_get_info": (Z, Z),
+        "fpssft_plan_get_lengths": (Z, Z, Z),
+        "fpssft_project": (Z, Z, Z, Z, Z, 1, Z, Z),
+        "fpssft_lines": (Z, Z, Z, Z, Z, 1, Z, Z),
+        "fpssft_recover": (Z,) * 12,
+        "fpssft_recover_host": (Z,) * 12,
+        "fpssft_synth": (Z, Z, Z, 1, Z, Z, Z, 0, Z, Z),
+        "fpssft_decode": (Z,) * 10,
+        "fpssft_finalize": (Z,) * 5,
+        "fpssft_adjoint": (Z, 0, Z, Z, Z, Z, 1, Z, Z, Z, Z),
+        "fpssft_probe_gather": (Z, 1024, 1, 256, 0, 0, Z, Z),
+        "fpssft_recover_noalloc": (2, 1, Z, Z) + (Z,) * 11,
+    }
+    for name, args in cases.items():
+        assert getattr(lib, name)(*args) == _lib.ERR_INVALID, name
+        assert lib.fpssft_last_error() != b"", name
+    lib.fpssft_plan_destroy(None)
