@@ -100,3 +100,19 @@ def test_every_call_rejects_a_null_plan_or_pointer_on_the_host():
         assert getattr(lib, name)(*args) == _lib.ERR_INVALID, name
         assert lib.fpssft_last_error() != b"", name
     lib.fpssft_plan_destroy(None)
+
+
+def test_a_missing_library_fails_loudly_instead_of_falling_back(tmp_path):
+    """No CPU fallback: with the CUDA library absent, loading it (the first step of every call)
+    raises FpssftError in a fresh process."""
+    import subprocess
+    import sys
+    code = ("from paper_1711_11407_gb300 import _lib\n"
+            f"_lib.use_library({str(tmp_path / 'missing.so')!r})\n"
+            "try:\n"
+            "    _lib.load()\n"
+            "except _lib.FpssftError as e:\n"
+            "    print('raised', e.status)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == f"raised {_lib.ERR_UNSUPPORTED}"
