@@ -75,7 +75,9 @@ def check_projection_slice(O, cases=None):
     if cases is None:
         cases = [((6, 10), [(1, 3), (0, 1), (4, 6), (0, 0), (5, 9)]),
                  ((4, 6, 3), [(1, 1, 1), (3, 0, 2), (2, 4, 0)]),
-                 ((5, 7), [(2, 3), (1, 0)])]
+                 ((5, 7), [(2, 3), (1, 0)]),
+                 ((9,), [(2,), (0,)]),
+                 ((2, 3, 2, 5), [(1, 1, 1, 1), (0, 2, 1, 3)])]
     for dims, slopes in cases:
         x = rng.normal(size=dims) + 1j * rng.normal(size=dims)
         X = np.fft.fftn(x) / x.size
@@ -241,7 +243,7 @@ def check_sparsity_tests(O):
 
 def check_tiny_support(O):
     rng = np.random.default_rng(13)
-    for dims, K in [((8, 8), 4), ((12, 18), 6), ((8, 8, 8), 6), ((6, 10), 3)]:
+    for dims, K in [((8, 8), 4), ((12, 18), 6), ((8, 8, 8), 6), ((6, 10), 3), ((16,), 3), ((2, 3, 2, 5), 4)]:
         for trial in range(3):
             ss = np.random.SeedSequence([17, trial, *dims])
             k, a, x, _, al, ta = S.make_signal(ss, dims, K, 60)
