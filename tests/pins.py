@@ -166,7 +166,7 @@ def check_uniform_projection(O):
 def check_single_sinusoid(O):
     rng = np.random.default_rng(5)
     p = O.Params(T=1, k_cap=4)
-    for dims in [(6, 10), (5, 7), (4, 6, 3), (8, 8)]:
+    for dims in [(6, 10), (5, 7), (4, 6, 3), (8, 8), (9,), (2, 3, 2, 5)]:
         for _ in range(3):
             k = tuple(int(rng.integers(0, n)) for n in dims)
             a = complex(rng.normal(), rng.normal())
