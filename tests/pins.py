@@ -274,6 +274,21 @@ def check_early_stop(O):
     assert full.history[-1][1] == 0, "the last iteration found no bin passing T0"
 
 
+# --- capacity: a full set drops new frequencies, flags the signal and stops it -------------------
+
+def check_capacity(O):
+    """30 planted frequencies into a set of 8: the run reports STATUS_CAPACITY, keeps at most 8
+    entries, all of them planted, and stops in the iteration that overflowed, before its budget."""
+    dims = (32, 32)
+    k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence(5), dims, 30, 10)
+    r = O.recover(x, al, ta, O.Params(T=10, k_cap=8))
+    assert r.status == O.STATUS_CAPACITY, "the overflow must be reported"
+    assert 0 < r.k.shape[0] <= 8
+    planted = set(O.linear_index(k, dims).tolist())
+    assert set(O.linear_index(r.k, dims).tolist()) <= planted
+    assert r.iters < 10, "an overflowing signal stops in that iteration"
+
+
 # --- a re-decoded frequency accumulates its residual (reading A9) ---------------------------------
 
 def check_redecode_accumulates(O):

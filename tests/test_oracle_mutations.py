@@ -29,6 +29,7 @@ CHECKS = [
     pins.check_projection_test,
     pins.check_sparsity_tests,
     pins.check_early_stop,
+    pins.check_capacity,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -154,6 +155,11 @@ def _classify_never_empty(bins, alpha, tau, dims, p):
     return cands, n0 + 1
 
 
+def _merge_hides_overflow(S, cands, k_cap):
+    _orig["merge"](S, cands, k_cap)
+    return True
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -175,6 +181,7 @@ MUTATIONS = {
     "grid test T2 dropped": ("classify_decode", _classify_without("eta")),
     "inverse line DFT loses the factor L": ("line_idft", _idft_unscaled),
     "early stop never fires": ("classify_decode", _classify_never_empty),
+    "a full set is not reported": ("merge", _merge_hides_overflow),
 }
 
 

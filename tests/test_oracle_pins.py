@@ -72,9 +72,7 @@ def test_literal_and_bins_peel_modes_recover_the_same_set():
 
 
 def test_capacity_overflow_sets_status():
-    k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence(5), (32, 32), 30, 10)
-    r = O.recover(x, al, ta, O.Params(T=10, k_cap=8))
-    assert r.status == O.STATUS_CAPACITY and r.k.shape[0] <= 8
+    pins.check_capacity(O)
 
 
 def test_resume_from_complete_set_stops_after_one_iteration():
