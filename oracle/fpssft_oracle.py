@@ -198,6 +198,17 @@ def projects_to(m, k, alpha, dims):
     return int(bin_index(np.asarray(k), alpha, dims)) == int(m)
 
 
+def decoded_amplitude(bins, m, k, tau, dims, average=False):
+    """Eq. decoding: a = s_0(m) times the conjugate of line 0's offset phase.  With `average`
+    (reading A12, for noisy data) the mean over the D+1 lines of s_j(m) times the conjugate of line
+    j's offset phase: every line carries the same amplitude times its own phase (Eq. freqSum)."""
+    kk = np.asarray(k)
+    if not average:
+        return complex(bins[0][m] * np.conj(line_phase(kk, tau, dims, 0)))
+    n = len(dims) + 1
+    return complex(sum(bins[j][m] * np.conj(line_phase(kk, tau, dims, j)) for j in range(n)) / n)
+
+
 def classify_decode(bins, alpha, tau, dims, p):
     """Decode every bin that passes the 1-sparsity tests.
 
@@ -239,11 +250,8 @@ def classify_decode(bins, alpha, tau, dims, p):
             continue
         if not projects_to(m, k, alpha, dims):
             continue
-        a = s0[m] * np.conj(line_phase(np.asarray(k), tau, dims, 0))
-        if p.amp_average:
-            # every line carries the same amplitude times its own offset phase (Eq. freqSum)
-            a = sum(bins[j][m] * np.conj(line_phase(np.asarray(k), tau, dims, j)) for j in range(D + 1)) / (D + 1)
-        out.append((int(m), tuple(int(v) for v in k), complex(a)))
+        a = decoded_amplitude(bins, m, k, tau, dims, p.amp_average)
+        out.append((int(m), tuple(int(v) for v in k), a))
     return out, int(np.count_nonzero(t0))
 
 

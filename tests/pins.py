@@ -289,6 +289,34 @@ def check_capacity(O):
     assert r.iters < 10, "an overflowing signal stops in that iteration"
 
 
+# --- amplitude from line 0 or averaged over the D+1 lines (Eq. decoding, reading A12) -------------
+
+def check_amplitude_average(O):
+    """Every line carries the same amplitude times its own offset phase (Eq. freqSum), so averaging
+    the D+1 phase-corrected bins returns the exact amplitude on a 1-sparse bin and divides the
+    variance of white bin noise by D+1."""
+    rng = np.random.default_rng(8)
+    dims = (32, 48)
+    k = np.asarray([(5, 17)])
+    a = np.asarray([0.8 - 0.6j])
+    x = S.synthesize_cube(dims, k, a)
+    errs = {False: [], True: []}
+    for _ in range(300):
+        alpha = [int(rng.integers(0, n)) for n in dims]
+        tau = [int(rng.integers(0, n)) for n in dims]
+        bins = O.project(x, alpha, tau)
+        for avg in (False, True):
+            cands, _ = O.classify_decode(bins, alpha, tau, dims, O.Params(amp_average=avg))
+            assert len(cands) == 1 and abs(cands[0][2] - a[0]) < 1e-12
+        noisy = bins + 0.02 * (rng.normal(size=bins.shape) + 1j * rng.normal(size=bins.shape))
+        for avg in (False, True):
+            cands, _ = O.classify_decode(noisy, alpha, tau, dims, O.Params(rho=0.25, eta=0.25, amp_average=avg))
+            if cands and cands[0][1] == tuple(k[0]):
+                errs[avg].append(abs(cands[0][2] - a[0]) ** 2)
+    ratio = np.mean(errs[True]) / np.mean(errs[False])
+    assert 0.2 < ratio < 0.5, f"variance ratio {ratio:.3f}, expected about 1/3 for D = 2"
+
+
 # --- a re-decoded frequency accumulates its residual (reading A9) ---------------------------------
 
 def check_redecode_accumulates(O):

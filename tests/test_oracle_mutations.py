@@ -30,6 +30,7 @@ CHECKS = [
     pins.check_sparsity_tests,
     pins.check_early_stop,
     pins.check_capacity,
+    pins.check_amplitude_average,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -160,6 +161,14 @@ def _merge_hides_overflow(S, cands, k_cap):
     return True
 
 
+def _average_with_line0_phase(bins, m, k, tau, dims, average=False):
+    # every line corrected by line 0's offset phase (the e_d shift of lines 1..D forgotten)
+    if not average:
+        return _orig["decoded_amplitude"](bins, m, k, tau, dims, False)
+    ph0 = np.conj(O.line_phase(np.asarray(k), tau, dims, 0))
+    return complex(sum(bins[j][m] for j in range(len(dims) + 1)) * ph0 / (len(dims) + 1))
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -182,6 +191,7 @@ MUTATIONS = {
     "inverse line DFT loses the factor L": ("line_idft", _idft_unscaled),
     "early stop never fires": ("classify_decode", _classify_never_empty),
     "a full set is not reported": ("merge", _merge_hides_overflow),
+    "averaged amplitude ignores the lines' own offset phases": ("decoded_amplitude", _average_with_line0_phase),
 }
 
 
