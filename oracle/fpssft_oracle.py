@@ -22,7 +22,13 @@ Readings of points the paper leaves open (each one is stated where it is used):
     the literal IDFT-subtract-DFT order is kept as `peel_mode="literal"`;
   * a frequency decoded again accumulates its amplitude; entries with |a| <= theta0 are dropped at
     output; the output is sorted by linear frequency index;
-  * optional early stop when no bin of line 0 passes T0 after peeling.
+  * optional early stop when no bin of line 0 passes T0 after peeling;
+  * optional amplitude averaged over the D+1 phase-corrected lines (`decoded_amplitude`);
+  * a full set (k_cap entries) drops new frequencies, flags the signal and stops it.
+
+Every function here is pinned by tests/pins.py against the paper's closed forms, brute force or
+printed values.  Parity unpinned: the outcome on noisy inputs, which the paper does not model; on
+those the CUDA path is compared with this oracle one iteration at a time from the same set.
 """
 from __future__ import annotations
 
