@@ -26,3 +26,23 @@ def test_cache_key_ignores_batch_order_and_size():
     assert a == b
     assert a != autotune.cache_key(np.array([[64, 64]]), p, "GB300")
     assert a != autotune.cache_key(np.array([[64, 64], [128, 128]]), Params(T=0, k_cap=256), "GB300")
+
+
+def test_cache_hit_returns_the_stored_choice_without_timing(tmp_path, monkeypatch):
+    """A batch whose shapes, budget and capacity were tuned before on this GPU takes the stored
+    launch choice from the JSON cache; nothing is launched (here: no device at all)."""
+    import json
+
+    import torch
+
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=None: "GB300 (test)")
+    dims = np.asarray([[64, 64], [128, 128], [64, 64]])
+    p = Params(T=0, k_cap=512)
+    key = autotune.cache_key(dims, p, "GB300 (test)")
+    path = tmp_path / "tune.json"
+    stored = {"choice": {"fft_path": 2, "gather_mode": 1, "threads": 96}, "timings": {"path=2": 0.2}}
+    path.write_text(json.dumps({key: stored}))
+    best, timings = autotune.tune(dims, p, torch.zeros(4, dtype=torch.complex64), None, None, None,
+                                  cache_path=str(path))
+    assert (best.fft_path, best.gather_mode, best.threads, best.k_cap) == (2, 1, 96, 512)
+    assert timings == stored["timings"]
