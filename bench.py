@@ -95,6 +95,21 @@ def stratified(wl, n, seed=0):
     return out[:max(n, len(groups))]
 
 
+def same_sets(ref, other, amp_tol=1e-4):
+    """True when two RecoverOutputs hold the same recovered sets: count, iterations and status
+    equal, and per signal the first count rows of k equal and of a within amp_tol relative."""
+    import torch
+    r = {f: getattr(ref, f).cpu() for f in ("k", "a", "count", "iters", "status")}
+    o = {f: getattr(other, f).cpu() for f in ("k", "a", "count", "iters", "status")}
+    if not all(torch.equal(r[f], o[f]) for f in ("count", "iters", "status")):
+        return False
+    rows = torch.arange(r["k"].shape[1])[None, :] < r["count"][:, None].long()
+    if not torch.equal(r["k"][rows], o["k"][rows]):
+        return False
+    ra, oa = r["a"][rows], o["a"][rows]
+    return bool(torch.all(torch.abs(ra - oa) <= amp_tol * torch.abs(ra)))
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -507,10 +522,14 @@ def main():
                 a1.record(stream)
                 a1.synchronize()
                 e2e_ms.append(a0.elapsed_time(a1))
+        same = same_sets(out, h_out)        # the last fpssft_recover_host run against the timed device run
         # end to end with the cubes left in pinned host memory (read in place over the host link):
         # per step the offsets and schedule are copied in and the outputs copied out
         d_offs, d_alpha, d_tau = torch.empty_like(offs), torch.empty_like(alpha), torch.empty_like(tau)
         m_out = plan.alloc_output(dev)
+        hm_out = plan.alloc_output("cpu")
+        for f in ("k", "a", "count", "iters", "status"):
+            setattr(hm_out, f, getattr(hm_out, f).pin_memory())
         with torch.cuda.stream(stream):
             def mapped_step():
                 d_offs.copy_(h_offs, non_blocking=True)
@@ -518,7 +537,7 @@ def main():
                 d_tau.copy_(h_tau, non_blocking=True)
                 plan.recover_mapped(h_cubes, d_offs, d_alpha, d_tau, out=m_out, stream=stream)
                 for f in ("k", "a", "count", "iters", "status"):
-                    getattr(h_out, f).copy_(getattr(m_out, f), non_blocking=True)
+                    getattr(hm_out, f).copy_(getattr(m_out, f), non_blocking=True)
             mapped_step()
             stream.synchronize()
             map_ms = []
@@ -529,9 +548,8 @@ def main():
                 a1.record(stream)
                 a1.synchronize()
                 map_ms.append(a0.elapsed_time(a1))
-        mapped_same = bool(torch.equal(h_out.count, out.count.cpu()))
+        mapped_same = same_sets(out, hm_out)
         e2e_step = max_over_ranks(sum(e2e_ms), world, dev) / args.steps
-        same = bool(torch.equal(h_out.count, out.count.cpu()))
         h2d = sum(int(x.numel() * x.element_size()) for x in (h_cubes, h_offs, h_alpha, h_tau))
         d2h = sum(int(getattr(h_out, f).numel() * getattr(h_out, f).element_size()) for f in ("k", "a", "count", "iters", "status"))
         line["e2e"] = {"value": job_rate(wl.batch, world, e2e_step), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -242,11 +242,17 @@ fpssft_status fpssft_adjoint(fpssft_plan_t plan, fpssft_adj_mode mode, const voi
  *     tau are [batch][T_max][D] with T_max = params->T when T > 0, else the largest per-signal
  *     budget floor(N_b / ((D+1) L_b)).
  * Limits: the tables must fit the array -- about 12 bytes per signal plus one 8-byte twiddle per
- * line position of every distinct line length, and at most 64 distinct shapes; larger requests
- * return FPSSFT_ERR_UNSUPPORTED with a message and launch nothing.
+ * line position of every distinct line length, and at most 64 distinct shapes.  The call always
+ * runs the one-CTA-per-signal kernel with the D+1 lines, their FFT partner and the recovered set
+ * in shared memory, so 16 (D+1) L_max + (12 + 4 D) k_cap + 8 H bytes (H the power of two >= 2 k_cap;
+ * plus the twiddles when they fit) must stay within one CTA's 227 KB; the plan-based
+ * fpssft_recover has global-memory variants for larger lines or sets, this call has none.
+ * Requests beyond either limit return FPSSFT_ERR_UNSUPPORTED with a message and launch nothing.
  * The first call on a device also looks up the array's device address and raises the recovery
- * kernel's shared-memory limit; make that first call before any stream capture.  The call copies
- * the tables into the array and clears the work counter on `stream` before the launch.
+ * kernel's shared-memory limit; make that first call before any stream capture.  The tables reach
+ * the array inside the parameters of small copy kernels launched on `stream` before the recovery
+ * (one per 32 000 bytes; the first also clears the work counter), so the call reads no host memory
+ * after it returns and does not wait for work already queued on `stream`.
  * Every call shares the one array and it keeps the last call's contents, so calls whose work
  * overlaps on the GPU (different streams, or different host threads) race: issue them one after
  * another on one stream. */

@@ -1038,6 +1038,25 @@ unsigned char* g_noalloc_dev[kNoallocMaxDevices] = {};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// The tables reach the array inside kernel parameters: the driver copies a launch's parameters
+// when the launch is issued, so the call reads no host memory after it returns and does not wait
+// for the stream's earlier work (a copy from pageable host memory would do both).  One launch
+// carries up to kUploadBytes (the parameter space holds 32 764 bytes); destinations and sizes
+// are multiples of 16 bytes.
+constexpr int kUploadBytes = 32000;
+
+struct UploadChunk {
+  uint4 data[kUploadBytes / 16];
+  uint4* dst;
+  int n16;              // 16-byte words to copy
+  int* clear;           // an int to set to zero first (nullable)
+};
+
+__global__ void __launch_bounds__(256) k_noalloc_upload(const __grid_constant__ UploadChunk c) {
+  if (c.clear != nullptr && threadIdx.x == 0) *c.clear = 0;
+  for (int i = threadIdx.x; i < c.n16; i += blockDim.x) c.dst[i] = c.data[i];
+}
+
 int factorize_into(int L, int* out) {
   int n = L, k = 0;
   const int small[] = {8, 4, 2, 3, 5};
@@ -1196,14 +1215,21 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
     while (threads < L_max && threads < 512) threads <<= 1;
   }
 
-  // ---- upload the tables and clear the work counter (no allocation: copies into the array) -----
-  const size_t bytes = off_tw + tw_used * sizeof(float2);
+  // ---- upload the tables and clear the work counter (no allocation: kernel parameters) ----------
+  const size_t bytes = (off_tw + tw_used * sizeof(float2) + 15) & ~size_t(15);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  FPSSFT_CUDA_TRY(cudaMemcpyAsync(dscratch + off_shapes, g_noalloc_host + off_shapes, bytes - off_shapes,
-                                  cudaMemcpyHostToDevice, s));
-  FPSSFT_CUDA_TRY(cudaMemsetAsync(dscratch + off_counter, 0, sizeof(int), s));
+  for (size_t at = off_shapes; at < bytes; at += kUploadBytes) {
+    static UploadChunk chunk;   // static: 32 KB is too much for the caller's stack; under the mutex
+    const size_t n = std::min((size_t)kUploadBytes, bytes - at);
+    std::memcpy(chunk.data, g_noalloc_host + at, n);
+    chunk.dst = reinterpret_cast<uint4*>(dscratch + at);
+    chunk.n16 = (int)(n / 16);
+    chunk.clear = at == off_shapes ? reinterpret_cast<int*>(dscratch + off_counter) : nullptr;
+    k_noalloc_upload<<<1, 256, 0, s>>>(chunk);
+    FPSSFT_CUDA_TRY(cudaGetLastError());
+  }
 
-  RecoverArgs A;
+  RecoverArgs A{};
   A.cubes = static_cast<const float2*>(cubes);
   A.offsets = offsets;
   A.alpha = alpha;

@@ -99,3 +99,40 @@ def test_clock_summary_keeps_this_gpu_inside_the_timed_region():
     assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     cs.t0, cs.t1 = 20.0, 21.0
     assert cs.summary()["samples"] == 0
+
+
+def test_e2e_self_check_compares_whole_sets_not_counts():
+    """The bench line's matches_device_run flags: equal counts are not enough -- a different
+    frequency, an amplitude off by more than 1e-4 relative or a different iteration count fails."""
+    import torch
+
+    from paper_1711_11407_gb300.api import RecoverOutput
+
+    def out():
+        k = torch.zeros((2, 4, 2), dtype=torch.int32)
+        k[0, :2] = torch.tensor([[1, 2], [3, 4]])
+        k[1, :1] = torch.tensor([[5, 6]])
+        a = torch.zeros((2, 4), dtype=torch.complex64)
+        a[0, :2] = torch.tensor([1 + 1j, 2 - 1j])
+        a[1, :1] = torch.tensor([0.5j])
+        return RecoverOutput(k, a, torch.tensor([2, 1], dtype=torch.int32), torch.tensor([3, 2], dtype=torch.int32),
+                             torch.zeros(2, dtype=torch.int32))
+
+    ref = out()
+    assert bench.same_sets(ref, out())
+    o = out()
+    o.k[2:] = 9                                  # rows beyond count are not part of the set
+    o.a[1, 3] = 7
+    assert bench.same_sets(ref, o)
+    o = out()
+    o.k[0, 1, 0] = 8
+    assert not bench.same_sets(ref, o)
+    o = out()
+    o.a[0, 0] *= 1 + 1e-3
+    assert not bench.same_sets(ref, o)
+    o = out()
+    o.a[0, 0] *= 1 + 1e-6
+    assert bench.same_sets(ref, o)
+    o = out()
+    o.iters[1] = 5
+    assert not bench.same_sets(ref, o)
