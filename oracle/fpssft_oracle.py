@@ -399,3 +399,49 @@ def synth_adjoint(g, k, alpha, tau, dims):
     for j in range(D + 1):
         out = out + np.conj(line_phase(k, tau, dims, j)) * g[j][m]
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Least-squares amplitudes over many lines (the refinement the library adds after the loop; the
+# paper's decode, Eq. decoding, reads each amplitude from one bin of one line)
+# ---------------------------------------------------------------------------------------------
+
+def refine_lstsq(x, alphas, taus, k, method="auto"):
+    """argmin_a sum_r || project(x, alpha_r, tau_r) - synth(k, a, alpha_r, tau_r) ||^2 in FP64.
+
+    The stacked system has one column per frequency k_i: the syntheses (Eq. freqSum) of a unit
+    amplitude at k_i on every row, and the right-hand side stacks the line DFTs of x (Eq. hs).
+    method "dense": numpy's least squares on the dense matrix; "sparse": the normal equations
+    A^H A a = A^H y solved directly (scipy) with A stored sparse (each column has one non-zero per
+    line and row); "auto": dense while the matrix has at most 4e6 entries."""
+    dims = [int(n) for n in x.shape]
+    D = len(dims)
+    k = np.asarray(k, np.int64).reshape(-1, D)
+    n = k.shape[0]
+    R = len(alphas)
+    y = np.concatenate([project(x, alphas[r], taus[r]).reshape(-1) for r in range(R)])
+    if n == 0:
+        return np.zeros(0, np.complex128)
+    if method == "auto":
+        method = "dense" if y.size * n <= 4_000_000 else "sparse"
+    rows, cols, vals = [], [], []
+    blk = y.size // R
+    for i in range(n):
+        e = np.zeros(n, np.complex128)
+        e[i] = 1.0
+        for r in range(R):
+            col = synth(k, e, alphas[r], taus[r], dims).reshape(-1)
+            nz = np.nonzero(col)[0]
+            rows.append(r * blk + nz)
+            cols.append(np.full(nz.size, i))
+            vals.append(col[nz])
+    rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    if method == "dense":
+        A = np.zeros((y.size, n), np.complex128)
+        np.add.at(A, (rows, cols), vals)
+        return np.linalg.lstsq(A, y, rcond=None)[0]
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(y.size, n))
+    AH = A.conj().T.tocsr()
+    return spla.spsolve((AH @ A).tocsc(), AH @ y)

@@ -413,6 +413,55 @@ def check_adjoints(O):
             assert abs(dre - grad[idx].real) < 1e-6 and abs(dim - grad[idx].imag) < 1e-6, "adjoint disagrees with FD"
 
 
+# --- least-squares amplitudes over many lines (the refinement after the loop) ----------------------
+
+def check_refine_lstsq(O):
+    """(1) Noiseless: the lines of x are exactly the syntheses of the planted set (Eq. freqSum), so
+    least squares on the planted support returns the planted amplitudes, by either solver, even
+    where frequencies share bins.  (2) One frequency: every line holds a times its offset phase
+    plus noise, so the least-squares amplitude is the mean over all rows and lines of the
+    phase-corrected bins.  (3) Noisy, several frequencies: the residual is orthogonal to every
+    column, checked through the synthesis adjoint (an independent code path), and the dense and
+    sparse solvers agree."""
+    rng = np.random.default_rng(31)
+    dims = (16, 24)
+    D = len(dims)
+    R = 6
+    alphas = [[int(rng.integers(0, n)) for n in dims] for _ in range(R)]
+    taus = [[int(rng.integers(0, n)) for n in dims] for _ in range(R)]
+    N = int(np.prod(dims))
+    k = grid(dims)[rng.choice(N, 40, replace=False)]
+    a = rng.normal(size=40) + 1j * rng.normal(size=40)
+    x = S.synthesize_cube(dims, k, a)
+    collide = any(len(set(O.bin_index(k, al, dims).tolist())) < len(k) for al in alphas)
+    assert collide, "the case must have frequencies sharing bins"
+    for method in ("dense", "sparse"):
+        got = O.refine_lstsq(x, alphas, taus, k, method=method)
+        assert np.allclose(got, a, atol=1e-9), f"{method}: noiseless least squares must return the planted amplitudes"
+    # (2) one frequency, noisy cube: the closed-form mean over the R (D+1) lines
+    k1 = np.asarray([(5, 17)])
+    a1 = np.asarray([0.7 + 0.2j])
+    xn = S.synthesize_cube(dims, k1, a1) + 0.3 * (rng.normal(size=dims) + 1j * rng.normal(size=dims))
+    mean = 0.0
+    for al, ta in zip(alphas, taus):
+        bins = O.project(xn, al, ta)
+        m = int(O.bin_index(k1, al, dims)[0])
+        for j in range(D + 1):
+            mean += bins[j][m] * np.conj(O.line_phase(k1, ta, dims, j)[0])
+    mean /= R * (D + 1)
+    for method in ("dense", "sparse"):
+        got = O.refine_lstsq(xn, alphas, taus, k1, method=method)
+        assert abs(got[0] - mean) < 1e-12, f"{method}: one frequency must give the mean of its phase-corrected bins"
+    # (3) noisy, 40 frequencies: normal equations through synth_adjoint, solvers agree
+    xn = x + 0.5 * (rng.normal(size=dims) + 1j * rng.normal(size=dims))
+    ad = O.refine_lstsq(xn, alphas, taus, k, method="dense")
+    asp = O.refine_lstsq(xn, alphas, taus, k, method="sparse")
+    assert np.allclose(ad, asp, atol=1e-9), "dense and sparse least squares disagree"
+    g = sum(O.synth_adjoint(O.project(xn, al, ta) - O.synth(k, ad, al, ta, dims), k, al, ta, dims)
+            for al, ta in zip(alphas, taus))
+    assert np.max(np.abs(g)) < 1e-9, "the least-squares residual must be orthogonal to every column"
+
+
 # --- Fig. 1 deadlock instance ----------------------------------------------------------------------
 
 def load_deadlock():

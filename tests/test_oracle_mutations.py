@@ -31,6 +31,7 @@ CHECKS = [
     pins.check_early_stop,
     pins.check_capacity,
     pins.check_amplitude_average,
+    pins.check_refine_lstsq,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -169,6 +170,32 @@ def _average_with_line0_phase(bins, m, k, tau, dims, average=False):
     return complex(sum(bins[j][m] for j in range(len(dims) + 1)) * ph0 / (len(dims) + 1))
 
 
+def _refine_line0_only(x, alphas, taus, k, method="auto"):
+    # least squares over line 0 of every row only (the offset lines forgotten)
+    dims = [int(n) for n in x.shape]
+    k = np.asarray(k, np.int64).reshape(-1, len(dims))
+    cols = []
+    for i in range(k.shape[0]):
+        e = np.zeros(k.shape[0], np.complex128)
+        e[i] = 1
+        cols.append(np.concatenate([O.synth(k, e, al, ta, dims)[0] for al, ta in zip(alphas, taus)]))
+    y = np.concatenate([O.project(x, al, ta)[0] for al, ta in zip(alphas, taus)])
+    return np.linalg.lstsq(np.stack(cols, axis=1), y, rcond=None)[0]
+
+
+def _refine_mean_of_decodes(x, alphas, taus, k, method="auto"):
+    # every amplitude taken as the mean of its phase-corrected bins, as if no two frequencies shared a bin
+    dims = [int(n) for n in x.shape]
+    k = np.asarray(k, np.int64).reshape(-1, len(dims))
+    acc = np.zeros(k.shape[0], np.complex128)
+    for al, ta in zip(alphas, taus):
+        bins = O.project(x, al, ta)
+        m = O.bin_index(k, al, dims)
+        for j in range(len(dims) + 1):
+            acc += bins[j][m] * np.conj(O.line_phase(k, ta, dims, j))
+    return acc / (len(alphas) * (len(dims) + 1))
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -192,6 +219,8 @@ MUTATIONS = {
     "early stop never fires": ("classify_decode", _classify_never_empty),
     "a full set is not reported": ("merge", _merge_hides_overflow),
     "averaged amplitude ignores the lines' own offset phases": ("decoded_amplitude", _average_with_line0_phase),
+    "least squares over line 0 only": ("refine_lstsq", _refine_line0_only),
+    "least squares replaced by the mean of the decodes": ("refine_lstsq", _refine_mean_of_decodes),
 }
 
 

@@ -153,3 +153,7 @@ def test_fig2_clustered_success_similar_to_uniform(block):
 
 def test_amplitude_averaged_over_lines_is_exact_noiseless_and_less_noisy():
     pins.check_amplitude_average(O)
+
+
+def test_least_squares_amplitudes_exact_noiseless_closed_form_and_normal_equations():
+    pins.check_refine_lstsq(O)
