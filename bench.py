@@ -57,6 +57,11 @@ def parse_args():
     ap.add_argument("--fft-path", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch configuration")
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1: leave)")
+    ap.add_argument("--refine-rows", type=int, default=0,
+                    help="after the timed recovery: least-squares amplitude refinement over this many schedule "
+                         "rows, on the recovered and on the planted support, timed, with its errors (0: off)")
+    ap.add_argument("--refine-iters", type=int, default=30)
+    ap.add_argument("--refine-oracle", type=int, default=2, help="signals checked against FP64 least squares")
     return ap.parse_args()
 
 
@@ -345,6 +350,79 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def refine_leg(args, wl, plan, cubes, offs, alpha, tau, out, stream):
+    """Least-squares amplitude refinement (fpssft_refine) after the recovery, over the first R
+    schedule rows: timed on the device (projection of the rows plus the CG loop, per batch), and
+    its amplitude errors against the planted amplitudes and against the oracle's FP64 least squares
+    on a few signals.  Run on the recovered support and on the planted support."""
+    import torch
+
+    from oracle import fpssft_oracle as O
+    R = min(args.refine_rows, int(alpha.shape[1]))
+    ra, rt = alpha[:, :R].contiguous(), tau[:, :R].contiguous()
+    dev = cubes.device
+    kp = torch.zeros_like(out.k)
+    cp = torch.zeros_like(out.count)
+    for b in range(wl.batch):
+        n = len(wl.k_true[b])
+        kp[b, :n] = torch.from_numpy(wl.k_true[b].astype(np.int32))
+        cp[b] = n
+    supports = {"recovered": (out.k, out.a.clone(), out.count), "planted": (kp, torch.zeros_like(out.a), cp)}
+    ws = torch.empty(plan.refine_workspace_bytes(), dtype=torch.uint8, device=dev)
+    resid = torch.empty(wl.batch, dtype=torch.float32, device=dev)
+    y = torch.empty((wl.batch, R, wl.D + 1, plan.L_max), dtype=torch.complex64, device=dev)
+    rec = {"rows": R, "cg_iterations": args.refine_iters,
+           "samples_fraction_of_cube": float(np.mean(R * (wl.D + 1) * plan.L / np.prod(wl.dims.astype(np.float64), axis=1)))}
+    for label, (k, a0, cnt) in supports.items():
+        a = torch.empty_like(a0)
+        with torch.cuda.stream(stream):
+            def run():
+                a.copy_(a0)
+                plan.project(cubes, offs, ra, rt, out=y, stream=stream)
+                plan.refine(y, ra, rt, k, a, cnt, iters=args.refine_iters, workspace=ws, resid=resid, stream=stream)
+            run()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ah = a.cpu().numpy()
+        a0h = a0.cpu().numpy()
+        kh = k.cpu().numpy()
+        ch = cnt.cpu().numpy()
+        rel_ref, rel_dec, n_common, n_total = [], [], 0, 0
+        for b in range(wl.batch):
+            truth = dict(zip(map(tuple, wl.k_true[b].tolist()), wl.a_true[b]))
+            n = int(ch[b])
+            n_total += n
+            for i in range(n):
+                t = truth.get(tuple(int(v) for v in kh[b, i]))
+                if t is None:
+                    continue
+                n_common += 1
+                rel_ref.append(abs(ah[b, i] - t) / abs(t))
+                if label == "recovered":
+                    rel_dec.append(abs(a0h[b, i] - t) / abs(t))
+        vs_oracle = []
+        for b in [b for b in range(wl.batch) if ch[b] > 0][:args.refine_oracle]:
+            n = int(ch[b])
+            ref = O.refine_lstsq(wl.cube(b), wl.alpha[b, :R], wl.tau[b, :R], kh[b, :n].astype(np.int64))
+            vs_oracle.append(float(np.linalg.norm(ah[b, :n] - ref) / np.linalg.norm(ref)))
+        med = lambda v: float(np.median(v)) if v else None
+        rec[label] = {"ms_per_batch": ms, "signals_per_s": wl.batch / (ms / 1000.0), "entries": n_total,
+                      "entries_in_planted_support": n_common,
+                      "refined_rel_error_vs_planted_median": med(rel_ref),
+                      "refined_rel_error_vs_planted_p90": float(np.percentile(rel_ref, 90)) if rel_ref else None,
+                      "rel_l2_vs_fp64_least_squares": vs_oracle}
+        if label == "recovered":
+            rec[label]["decoded_rel_error_vs_planted_median"] = med(rel_dec)
+    return rec
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -486,6 +564,8 @@ def main():
                                       "ceiling_ms": 1000.0 * t_ceiling, "frac": 1000.0 * t_ceiling / ms_per_step,
                                       "probe": "fpssft_probe_gather, 4 GiB buffer, 9.7M threads x 64 random reads"}
 
+    refine_rec = refine_leg(args, wl, plan, cubes, offs, alpha, tau, out, stream) if args.refine_rows > 0 else None
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -502,6 +582,8 @@ def main():
             # samples read per signal as a fraction of its cube: iterations (D+1) L / N (Sec. 3's measure)
             "mean_sample_fraction": float(np.mean(it64 * (wl.D + 1) * L / np.prod(wl.dims.astype(np.float64), axis=1))),
             "clocks": clk.summary()}
+    if refine_rec is not None:
+        line["refine"] = refine_rec
 
     if not args.quick:
         # ---- end to end through the host-buffer call ------------------------------------------

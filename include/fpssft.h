@@ -226,6 +226,34 @@ fpssft_status fpssft_adjoint(fpssft_plan_t plan, fpssft_adj_mode mode, const voi
                              int n_sched, const int32_t* k, const int32_t* count, void* grad_out,
                              void* stream);
 
+/* Least-squares amplitude refinement on a fixed support.  The decode (Sec. 2.2, Eq. decoding)
+ * reads each amplitude from one bin of one line; over n_sched schedule rows every line carries
+ * the same amplitudes (Eq. freqSum), y_r = S_r a + noise, with y_r the D+1 line DFTs of row r
+ * (Eq. sample_slice, Eq. hs) and S_r the synthesis of fpssft_synth.  This call solves, per signal,
+ *     min_a  sum_r || y_r - S_r a ||^2
+ * by conjugate gradients on the normal equations (S^H S) a = S^H y (the least-squares step is an
+ * addition of this library; the paper stops at the decode).  Everything runs on the device, two
+ * launches per iteration and none of them waits on the host; signals whose normal-equation
+ * residual falls below tol^2 of its start stop changing (later iterations leave them as they are).
+ *   bins:      device complex64 [batch][n_sched][D+1][L_max], y = fpssft_project of the cubes on the
+ *              same rows;
+ *   alpha, tau: device int32 [batch][n_sched][D], the rows;
+ *   k, count:  device, the support (entries i < count[b] of k [batch][k_cap][D]; entries off the
+ *              grid are ignored);
+ *   a:         device complex64 [batch][k_cap]: the starting amplitudes on entry, the refined ones on
+ *              return (entries i >= count[b] untouched);
+ *   iters:     conjugate-gradient iterations (0: only the residual);
+ *   workspace: device, at least fpssft_refine_workspace_size bytes, 256-byte aligned, owned by the
+ *              caller (contents need no initialisation; overwritten);
+ *   resid:     nullable device float [batch]: || y - S a || over all rows after the last iteration.
+ * Arithmetic: FP32 vectors and bins, FP64 CG scalars.  FPSSFT_ERR_UNSUPPORTED when the D+1 lines
+ * of one row do not fit one CTA's shared memory. */
+fpssft_status fpssft_refine_workspace_size(fpssft_plan_t plan, size_t* bytes);
+fpssft_status fpssft_refine(fpssft_plan_t plan, const void* bins, const int32_t* alpha, const int32_t* tau,
+                            int n_sched, const int32_t* k, const int32_t* count, void* a, int iters,
+                            float tol, void* workspace, size_t workspace_bytes, float* resid,
+                            void* stream);
+
 /* Size of the fixed device scratch used by fpssft_recover_noalloc (bytes). */
 #define FPSSFT_NOALLOC_SCRATCH_BYTES (1 << 20)
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfpssft.so")
 SOURCES = [os.path.join(_HERE, "csrc", "fpssft.cu")]
 DEPENDS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("fpssft_device.cuh", "recover_common.cuh",
                                                                 "recover_shared.cuh", "recover_warp.cuh",
-                                                                "recover_cluster.cuh", "aux_kernels.cuh",
+                                                                "recover_cluster.cuh", "aux_kernels.cuh", "refine.cuh",
                                                                 "phase_timers.cuh")] + \
     [os.path.join(_ROOT, "include", "fpssft.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -105,6 +105,8 @@ SIGNATURES = {
     "fpssft_decode": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fpssft_finalize": (_I, [_P, _P, _P, _P, _P]),
     "fpssft_adjoint": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
+    "fpssft_refine_workspace_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "fpssft_refine": (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _I, ctypes.c_float, _P, ctypes.c_size_t, _P, _P]),
     "fpssft_probe_gather": (_I, [_P, ctypes.c_int64, _I, _I, _I, _I, _P, _P]),
     "fpssft_l2_fetch_granularity": (_I, [_I, ctypes.POINTER(ctypes.c_int)]),
     "fpssft_phase_read": (_I, [_P]),

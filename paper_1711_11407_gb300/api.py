@@ -276,6 +276,31 @@ class Plan:
                                            _ptr(tau), S, _ptr(k), _ptr(count), _ptr(grad_a), _stream(stream)))
         return grad_a
 
+    def refine_workspace_bytes(self):
+        n = ctypes.c_size_t(0)
+        _lib.check(self.lib.fpssft_refine_workspace_size(self.handle, ctypes.byref(n)))
+        return int(n.value)
+
+    def refine(self, bins, alpha, tau, k, a, count, iters=25, tol=1e-7, workspace=None, resid=None, stream=None):
+        """Least-squares amplitudes on the support (k, count) over the rows alpha/tau, from the line
+        DFTs `bins` of those rows (fpssft_refine); `a` is refined in place.  Returns (a, resid)."""
+        S = self._sched(alpha, tau)
+        _need(bins, torch.complex64, "bins")
+        self._check_set(k, a, count)
+        if tuple(bins.shape) != self._bins_shape(S):
+            raise ValueError(f"bins must be {self._bins_shape(S)}")
+        nbytes = self.refine_workspace_bytes()
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=bins.device)
+        _need(workspace, torch.uint8, "workspace")
+        if resid is None:
+            resid = torch.empty(self.batch, dtype=torch.float32, device=bins.device)
+        _need(resid, torch.float32, "resid")
+        _lib.check(self.lib.fpssft_refine(self.handle, _ptr(bins), _ptr(alpha), _ptr(tau), S, _ptr(k), _ptr(count),
+                                          _ptr(a), int(iters), float(tol), _ptr(workspace),
+                                          workspace.numel(), _ptr(resid), _stream(stream)))
+        return a, resid
+
 
 def probe_gather(buf, reads_per_thread=64, threads_total=152 * 8 * 256, load_mode=0, pair=0, stream=None):
     """Random 8-byte gathers over `buf` (complex64 CUDA tensor, power-of-two length); returns the

@@ -10,9 +10,9 @@ scatter-add) and S^H g (gather-reduce), so these Functions differentiate through
 
 `refine` re-estimates the amplitudes of a recovered support by least squares over many lines:
 minimise sum_rows ||P x - S a||^2 over a (per signal), by conjugate gradients on the normal
-equations, with S a from the synthesis kernel and S^H r from its autograd backward.  The decode
-uses one bin of one line per frequency (Eq. decoding); the refinement averages the noise over
-every line of the schedule.
+equations S^H S a = S^H P x, whose operator the library applies in one fused kernel (S and S^H
+through shared-memory bins).  The decode uses one bin of one line per frequency (Eq. decoding);
+the refinement averages the noise over every line of the schedule.
 """
 from __future__ import annotations
 
@@ -66,42 +66,12 @@ def sparse_synth(a, plan, k, count, alpha, tau):
     return SparseSynth.apply(a, plan, k, count, alpha, tau)
 
 
-def _adjoint_synth(plan, k, count, alpha, tau, r):
-    """S^H r through the autograd backward of SparseSynth."""
-    a = torch.zeros((plan.batch, plan.k_cap), dtype=torch.complex64, device=r.device, requires_grad=True)
-    y = sparse_synth(a, plan, k, count, alpha, tau)
-    (g,) = torch.autograd.grad(y, a, grad_outputs=r)
-    return g
-
-
-def refine(plan: Plan, cubes, offsets, k, a0, count, alpha, tau, iters=25, tol=1e-7):
+def refine(plan: Plan, cubes, offsets, k, a0, count, alpha, tau, iters=25, tol=1e-7, stream=None):
     """Least-squares amplitudes on a fixed support, per signal: argmin_a sum ||P x - S a||^2 over the
-    schedule rows alpha/tau [batch][n_sched][D].  Returns (a, residual norms per signal)."""
-    mask = (torch.arange(plan.k_cap, device=a0.device)[None, :] < count[:, None].long())
-    y = line_project(cubes, plan, offsets, alpha, tau).detach()
-    a = (a0 * mask).detach().clone()
-
-    def S(v):
-        return sparse_synth(v, plan, k, count, alpha, tau).detach()
-
-    def dot(u, v):       # per-signal <u, v> over all but the batch axis
-        return torch.sum((u.conj() * v).reshape(u.shape[0], -1), dim=1)
-
-    r = _adjoint_synth(plan, k, count, alpha, tau, y - S(a)) * mask       # S^H (y - S a)
-    p = r.clone()
-    rr = dot(r, r).real
-    rr0 = rr.clone()
-    for _ in range(iters):
-        q = S(p)
-        qq = dot(q, q).real
-        step = torch.where(qq > 0, rr / torch.clamp(qq, min=1e-30), torch.zeros_like(qq))
-        a = a + step[:, None] * p
-        r = r - step[:, None] * (_adjoint_synth(plan, k, count, alpha, tau, q) * mask)
-        rr_new = dot(r, r).real
-        beta = torch.where(rr > 0, rr_new / torch.clamp(rr, min=1e-30), torch.zeros_like(rr))
-        p = r + beta[:, None] * p
-        rr = rr_new
-        if bool(torch.all(rr <= tol * tol * torch.clamp(rr0, min=1e-30))):
-            break
-    res = torch.sqrt(dot(y - S(a), y - S(a)).real)
-    return a.detach(), res
+    schedule rows alpha/tau [batch][n_sched][D].  The line DFTs P x come from the projection kernel
+    and the conjugate-gradient loop runs in the library (fpssft_refine: two launches per iteration,
+    no host synchronisation, so the call can sit inside a captured CUDA graph).
+    Returns (a, residual norms ||P x - S a|| per signal)."""
+    y = plan.project(cubes, offsets, alpha, tau, stream=stream)
+    a = a0.detach().clone()
+    return plan.refine(y, alpha, tau, k, a, count, iters=iters, tol=tol, stream=stream)

@@ -90,6 +90,7 @@ cudaError_t ensure_dynamic_smem(const void* func, size_t bytes) {
 #include "recover_warp.cuh"
 #include "recover_cluster.cuh"
 #include "aux_kernels.cuh"
+#include "refine.cuh"
 
 // ================================================================================================
 // Host side: plan
@@ -107,6 +108,7 @@ struct fpssft_plan_s {
   int threads = 256;
   int grid = 1;
   int sm_count = 1;
+  int smem_optin = 227 * 1024;   // opt-in shared memory per CTA of the plan's device
   bool tw_smem = true;
   bool prefetch = true;
   bool warp_path = false;   // k_recover_w (register FFT per line) instead of k_recover
@@ -354,6 +356,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (optin <= 0) optin = 227 * 1024;
   if (sms <= 0) sms = 1;
   P->sm_count = sms;
+  P->smem_optin = optin;
   const size_t static_reserve = sizeof(Shape) + 256;
   // the register-FFT path applies when every line length is 32 R with R in {1, 2, 4, 8}
   bool warp_ok = true;
@@ -924,6 +927,115 @@ extern "C" fpssft_status fpssft_adjoint(fpssft_plan_t P, fpssft_adj_mode mode, c
     constexpr int DD = decltype(Dc)::value;
     k_adjoint_synth<DD><<<grid, 256, 0, s>>>(A);
     FPSSFT_CUDA_TRY(cudaGetLastError());
+    return FPSSFT_OK;
+  });
+}
+
+// ---- least-squares amplitude refinement ---------------------------------------------------------
+namespace {
+struct RefineLayout {
+  size_t r, p, g, sc, total;
+};
+RefineLayout refine_layout(int batch, int k_cap) {
+  auto al = [](size_t v) -> size_t { return (v + 255) & ~size_t(255); };
+  RefineLayout w{};
+  const size_t vec = (size_t)batch * k_cap * sizeof(float2);
+  w.r = 0;
+  w.p = al(w.r + vec);
+  w.g = al(w.p + vec);
+  w.sc = al(w.g + vec);
+  w.total = al(w.sc + (size_t)batch * sizeof(RefineScalars));
+  return w;
+}
+}  // namespace
+
+extern "C" fpssft_status fpssft_refine_workspace_size(fpssft_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return fail(FPSSFT_ERR_INVALID, "null plan or output");
+  *bytes = refine_layout(P->batch, P->p.k_cap).total;
+  return FPSSFT_OK;
+}
+
+extern "C" fpssft_status fpssft_refine(fpssft_plan_t P, const void* bins, const int32_t* alpha, const int32_t* tau,
+                                       int n_sched, const int32_t* k, const int32_t* count, void* a, int iters,
+                                       float tol, void* workspace, size_t workspace_bytes, float* resid,
+                                       void* stream) {
+  if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
+  if (n_sched < 0 || iters < 0) return fail(FPSSFT_ERR_INVALID, "n_sched and iters must be >= 0");
+  if (!(tol >= 0.f)) return fail(FPSSFT_ERR_INVALID, "tol must be >= 0");
+  if (P->batch == 0) return FPSSFT_OK;
+  if (!bins || !alpha || !tau || !k || !count || !a || !workspace) return fail(FPSSFT_ERR_INVALID, "null device pointer");
+  const RefineLayout w = refine_layout(P->batch, P->p.k_cap);
+  if (workspace_bytes < w.total) return fail(FPSSFT_ERR_INVALID, "workspace smaller than fpssft_refine_workspace_size");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return fail(FPSSFT_ERR_INVALID, "workspace must be 256-byte aligned");
+  const size_t lines = (size_t)(P->D + 1) * P->L_max * sizeof(float2);
+  const size_t with_g = lines + (size_t)P->p.k_cap * sizeof(float2);
+  const size_t reserve = sizeof(Shape) + 512;
+  if (lines + reserve > (size_t)P->smem_optin) return fail(FPSSFT_ERR_UNSUPPORTED, "lines of this plan exceed one CTA's shared memory");
+  const bool g_in_smem = with_g + reserve <= (size_t)P->smem_optin;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  float2* r = reinterpret_cast<float2*>(ws + w.r);
+  float2* pv = reinterpret_cast<float2*>(ws + w.p);
+  float2* g = reinterpret_cast<float2*>(ws + w.g);
+  RefineScalars* sc = reinterpret_cast<RefineScalars*>(ws + w.sc);
+  FPSSFT_CUDA_TRY(cudaMemsetAsync(ws + w.g, 0, w.total - w.g, s));
+
+  RefineNormalArgs N{};
+  N.y = static_cast<const float2*>(bins);
+  N.alpha = alpha;
+  N.tau = tau;
+  N.n_sched = n_sched;
+  N.tab = P->tables();
+  N.batch = P->batch;
+  N.L_max = P->L_max;
+  N.k_cap = P->p.k_cap;
+  N.k = k;
+  N.count = count;
+  N.g = g;
+  N.sc = sc;
+  N.g_in_smem = g_in_smem ? 1 : 0;
+  // rows split so that about four CTAs per SM have work
+  const long long want = (long long)P->sm_count * 4;
+  const int ups = (int)std::max(1LL, std::min<long long>(n_sched, (want + P->batch - 1) / P->batch));
+  N.units_per_signal = ups;
+  N.rows_per_unit = n_sched > 0 ? (n_sched + ups - 1) / ups : 1;
+  const int ngrid = unit_grid(P, (long long)P->batch * ups, 8);
+  const size_t nsm = g_in_smem ? with_g : lines;
+  RefineUpdateArgs U{};
+  U.batch = P->batch;
+  U.k_cap = P->p.k_cap;
+  U.count = count;
+  U.a = static_cast<float2*>(a);
+  U.r = r;
+  U.p = pv;
+  U.g = g;
+  U.sc = sc;
+  U.resid = resid;
+  U.tol2 = (double)tol * (double)tol;
+  const int ugrid = unit_grid(P, P->batch, 8);
+  return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
+    constexpr int DD = decltype(Dc)::value;
+    FPSSFT_CUDA_TRY(ensure_dynamic_smem((const void*)k_refine_normal<DD>, nsm));
+    auto normal = [&](int mode, const float2* v, int want_g) -> cudaError_t {
+      N.mode = mode;
+      N.v = v;
+      N.want_g = want_g;
+      k_refine_normal<DD><<<ngrid, 256, nsm, s>>>(N);
+      return cudaGetLastError();
+    };
+    auto update = [&](int mode) -> cudaError_t {
+      U.mode = mode;
+      k_refine_update<<<ugrid, 256, 0, s>>>(U);
+      return cudaGetLastError();
+    };
+    FPSSFT_CUDA_TRY(normal(0, U.a, 1));          // g = S^H (y - S a0)
+    FPSSFT_CUDA_TRY(update(0));                  // r = p = g
+    for (int it = 0; it < iters; ++it) {
+      FPSSFT_CUDA_TRY(normal(1, pv, 1));         // g = S^H S p, sq = ||S p||^2
+      FPSSFT_CUDA_TRY(update(1));
+    }
+    FPSSFT_CUDA_TRY(normal(0, U.a, 0));          // sq = ||y - S a||^2
+    FPSSFT_CUDA_TRY(update(2));
     return FPSSFT_OK;
   });
 }
