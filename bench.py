@@ -175,6 +175,15 @@ def profiled_traffic(workload, batch):
     return per_signal * batch, path
 
 
+def probe_dram_bytes():
+    """DRAM bytes per isolated random access at the probe's ceiling (committed ncu record), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "probe_gather_random_access.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region: the sampler starts before it
     (and its first line is awaited), every line is time-stamped on arrival, and the summary keeps
@@ -563,6 +572,17 @@ def main():
                                       "pairs_per_launch": pairs, "singles_per_launch": singles,
                                       "ceiling_ms": 1000.0 * t_ceiling, "frac": 1000.0 * t_ceiling / ms_per_step,
                                       "probe": "fpssft_probe_gather, 4 GiB buffer, 9.7M threads x 64 random reads"}
+        # the same ceiling in DRAM bytes: the probe moves a whole line per isolated access, while the
+        # kernel hits L2 for part of its samples, so compare the DRAM bytes each moves per second
+        probe_bytes = probe_dram_bytes()
+        if traffic is not None and probe_bytes is not None:
+            probe_gbs = (pairs * probe_bytes["dram_bytes_per_pair_access"]
+                         + singles * probe_bytes["dram_bytes_per_single_access"]) / t_ceiling / 1e9
+            kern_gbs = traffic / (ms_per_step / 1000.0) / 1e9
+            roofline["gather_ceiling"]["dram_view"] = {
+                "kernel_dram_gbs": kern_gbs, "probe_dram_gbs": probe_gbs, "frac": kern_gbs / probe_gbs,
+                "note": "kernel DRAM bytes per launch (roofline.traffic) per step time, against the DRAM bytes "
+                        "per second the probe moves for the same mix of single and pair accesses"}
 
     refine_rec = refine_leg(args, wl, plan, cubes, offs, alpha, tau, out, stream) if args.refine_rows > 0 else None
 
