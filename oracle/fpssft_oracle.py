@@ -445,3 +445,74 @@ def refine_lstsq(x, alphas, taus, k, method="auto"):
     A = sp.csr_matrix((vals, (rows, cols)), shape=(y.size, n))
     AH = A.conj().T.tocsr()
     return spla.spsolve((AH @ A).tocsc(), AH @ y)
+
+
+# ---------------------------------------------------------------------------------------------
+# Several offset sets per slope (an extension for noisy data; the paper samples one offset set,
+# tau and tau + e_d, per slope in each iteration, Sec. 2.2 and 2.3)
+# ---------------------------------------------------------------------------------------------
+
+def classify_decode_sets(bins_s, alpha, taus, dims, p):
+    """The tests and decode of `classify_decode` on S offset sets of one slope.
+
+    bins_s[s] are the (peeled) D+1 line DFTs at offset taus[s].  A frequency k in bin m appears in
+    every set with the same amplitude and with the offset phase of that set (Eq. freqSum), so the
+    ratio s_{s,d+1}(m) / s_{s,0}(m) is the same for every s.  With E_j = mean_s |s_{s,j}(m)|^2:
+      T0  sqrt(E_0) > theta0;   T1  |sqrt(E_{d+1}) - sqrt(E_0)| <= rho sqrt(E_0) for every d;
+      decode k_d from the phase of the coherent sum sum_s s_{s,d+1}(m) conj(s_{s,0}(m));  T2, T3 as
+      in `classify_decode`;  a = mean over the sets of s_{s,0}(m) times the conjugate offset phase
+      of line 0 (with p.amp_average: mean over sets and lines).
+    With one set this is `classify_decode`.  Returns (list of (m, k, a), number of bins passing T0)."""
+    dims = [int(n) for n in dims]
+    D = len(dims)
+    S = len(bins_s)
+    E = [np.mean([np.abs(bins_s[s][j]) ** 2 for s in range(S)], axis=0) for j in range(D + 1)]
+    mag0 = np.sqrt(E[0])
+    t0 = mag0 > p.theta0
+    out = []
+    for m in np.nonzero(t0)[0]:
+        if any(abs(math.sqrt(E[d + 1][m]) - mag0[m]) > p.rho * mag0[m] for d in range(D)):
+            continue
+        k = []
+        ok = True
+        for d in range(D):
+            r = sum(bins_s[s][d + 1][m] * np.conj(bins_s[s][0][m]) for s in range(S))
+            u = dims[d] * np.angle(r) / TWO_PI
+            q = math.floor(u + 0.5)
+            if abs(u - q) > p.eta:
+                ok = False
+                break
+            k.append(q % dims[d])
+        if not ok or not projects_to(m, k, alpha, dims):
+            continue
+        a = sum(decoded_amplitude(bins_s[s], m, k, taus[s], dims, p.amp_average) for s in range(S)) / S
+        out.append((int(m), tuple(int(v) for v in k), a))
+    return out, int(np.count_nonzero(t0))
+
+
+def recover_offset_sets(x, alpha, taus, p):
+    """`recover` with S offset sets per slope: iteration t samples the D+1 lines at slope alpha[t]
+    for each offset taus[t][s] (S (D+1) L samples), peels the recovered set from every set's bins
+    and decodes with `classify_decode_sets`.  Merge, early stop and output as in `recover`."""
+    dims = list(x.shape)
+    D = len(dims)
+    S = {}
+    status = STATUS_OK
+    iters = 0
+    for t in range(len(alpha)):
+        al = alpha[t]
+        ks = np.asarray(list(S.keys()), np.int64).reshape(-1, D)
+        as_ = np.asarray(list(S.values()), np.complex128)
+        bins_s = [peel_bins(project(x, al, ta), ks, as_, al, ta, dims) for ta in taus[t]]
+        cands, n_t0 = classify_decode_sets(bins_s, al, taus[t], dims, p)
+        iters = t + 1
+        if p.early_stop and n_t0 == 0:
+            break
+        if not merge(S, cands, p.k_cap):
+            status = STATUS_CAPACITY
+            break
+    keep = [(kk, aa) for kk, aa in S.items() if abs(aa) > p.theta0]
+    k = np.asarray([kk for kk, _ in keep], np.int64).reshape(-1, D)
+    a = np.asarray([aa for _, aa in keep], np.complex128)
+    order = np.argsort(linear_index(k, dims), kind="stable")
+    return Result(k[order], a[order], iters, status)

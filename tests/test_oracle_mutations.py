@@ -32,6 +32,7 @@ CHECKS = [
     pins.check_capacity,
     pins.check_amplitude_average,
     pins.check_refine_lstsq,
+    pins.check_offset_sets,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -196,6 +197,20 @@ def _refine_mean_of_decodes(x, alphas, taus, k, method="auto"):
     return acc / (len(alphas) * (len(dims) + 1))
 
 
+def _sets_phase_from_first(bins_s, alpha, taus, dims, p):
+    # the decode phase taken from the first offset set only (no coherent sum)
+    cands, n0 = _orig["classify_decode_sets"](bins_s[:1], alpha, taus[:1], dims, p)
+    full, n0_all = _orig["classify_decode_sets"](bins_s, alpha, taus, dims, p)
+    amp = {m: a for m, _, a in full}
+    return [(m, k, amp.get(m, a)) for m, k, a in cands], n0_all
+
+
+def _sets_amplitude_from_first(bins_s, alpha, taus, dims, p):
+    # the amplitude taken from the first offset set only
+    cands, n0 = _orig["classify_decode_sets"](bins_s, alpha, taus, dims, p)
+    return [(m, k, O.decoded_amplitude(bins_s[0], m, k, taus[0], dims, p.amp_average)) for m, k, _ in cands], n0
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -221,6 +236,8 @@ MUTATIONS = {
     "averaged amplitude ignores the lines' own offset phases": ("decoded_amplitude", _average_with_line0_phase),
     "least squares over line 0 only": ("refine_lstsq", _refine_line0_only),
     "least squares replaced by the mean of the decodes": ("refine_lstsq", _refine_mean_of_decodes),
+    "offset sets: phase from the first set only": ("classify_decode_sets", _sets_phase_from_first),
+    "offset sets: amplitude from the first set only": ("classify_decode_sets", _sets_amplitude_from_first),
 }
 
 

@@ -157,3 +157,7 @@ def test_amplitude_averaged_over_lines_is_exact_noiseless_and_less_noisy():
 
 def test_least_squares_amplitudes_exact_noiseless_closed_form_and_normal_equations():
     pins.check_refine_lstsq(O)
+
+
+def test_offset_sets_reduce_to_the_plain_loop_decode_exactly_and_average_the_noise():
+    pins.check_offset_sets(O)
