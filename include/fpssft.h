@@ -94,6 +94,13 @@ typedef struct {
                         one line plus the set fit one CTA's shared memory, else 1 */
   int amp_average;   /* 0: amplitude from line tau only (Eq. decoding); nonzero: the mean over the
                         D+1 lines of s_j times the conjugate of line j's offset phase (noisy data) */
+  int radix_plan;    /* order of the mixed-radix stages of the shared-memory FFT (paths 1 and 3; the
+                        result is the same DFT, only the stage sequence changes):
+                        0 = radix 8 as often as possible, then 4, 2, then 3, 5 and larger primes;
+                        1 = radix 4 first (then one 2), then the odd factors;
+                        2 = the odd factors (3, 5, larger primes) first, then 8, 4, 2;
+                        3 = the power of two as radix 8 and 4 stages only (no radix-2 stage unless
+                            L's power of two is 2), then the odd factors */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;
@@ -324,6 +331,13 @@ fpssft_status fpssft_l2_fetch_granularity(int bytes, int* previous);
 #define FPSSFT_PHASE_COUNT 7
 #define FPSSFT_PHASE_WORDS (FPSSFT_PHASE_COUNT + 4)
 fpssft_status fpssft_phase_read(int64_t* out);
+
+/* Host-only helper (no device work): the radix of each stage of the L-point mixed-radix FFT under
+ * radix plan `radix_plan` (fpssft_params.radix_plan), in the order the stages run.  radices: host,
+ * room for 24 entries; *n_stages receives their number.  The stages multiply to L (the L-point DFT
+ * of Eq. hs factored Cooley-Tukey style); FPSSFT_ERR_INVALID for L outside [1, 2^24] or an unknown
+ * plan, FPSSFT_ERR_UNSUPPORTED beyond 24 stages. */
+fpssft_status fpssft_fft_stages(int L, int radix_plan, int32_t* radices, int32_t* n_stages);
 
 /* Message of the last failed call on this thread ("" when none). */
 const char* fpssft_last_error(void);

@@ -85,7 +85,7 @@ class CParams(ctypes.Structure):
                 ("eta", ctypes.c_float), ("early_stop", ctypes.c_int), ("peel_mode", ctypes.c_int),
                 ("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("fp64_decisions", ctypes.c_int), ("gather_mode", ctypes.c_int), ("fft_path", ctypes.c_int),
-                ("amp_average", ctypes.c_int)]
+                ("amp_average", ctypes.c_int), ("radix_plan", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -111,6 +111,7 @@ SIGNATURES = {
     "fpssft_l2_fetch_granularity": (_I, [_I, ctypes.POINTER(ctypes.c_int)]),
     "fpssft_phase_read": (_I, [_P]),
     "fpssft_recover_noalloc": (_I, [_I, _I, _P, ctypes.POINTER(CParams), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fpssft_fft_stages": (_I, [_I, _I, _P, _P]),
     "fpssft_last_error": (ctypes.c_char_p, []),
     "fpssft_version": (ctypes.c_char_p, []),
 }

@@ -6,7 +6,10 @@ Candidates are the valid combinations of
                line, a cluster of D+1 CTAs per signal; only for lines of 512 points or more),
   gather_mode  1 (synchronous through L1), 2 (L2 only) or 3 (asynchronous prefetch: cp.async into
                shared memory; on path 2 it replaces the register prefetch),
-  threads      CTA size for paths 1 and 3 (path 2 is fixed at 32 (D+1)).
+  threads      CTA size for paths 1 and 3 (path 2 is fixed at 32 (D+1)),
+  radix_plan   the order of the shared-memory FFT's mixed-radix stages (paths 1 and 3): tried for
+               the fastest of the candidates above, each plan whose stage sequence differs from
+               the default for some line length of the batch (fpssft_fft_stages).
 Each candidate is timed on the caller's own inputs with CUDA events (warm-up first, a buffer larger
 than L2 written between timed launches); the fastest wins.  Results are cached in a JSON file keyed
 by GPU name, D, the sorted set of shapes, k_cap and T, so a batch with the same layout is not
@@ -59,6 +62,33 @@ def candidates(dims, params: Params):
     return out
 
 
+def fft_stages(L, radix_plan):
+    """Radices of the L-point FFT's stages under a radix plan (host-only library call)."""
+    import ctypes
+
+    from . import _lib
+    lib = _lib.load()
+    out = (ctypes.c_int32 * 24)()
+    n = ctypes.c_int32(0)
+    _lib.check(lib.fpssft_fft_stages(int(L), int(radix_plan), out, ctypes.byref(n)))
+    return [int(out[i]) for i in range(n.value)]
+
+
+def radix_candidates(dims, params: Params):
+    """The radix plans other than the default that change some line length's stage sequence, for
+    the shared-memory FFT paths (host logic only)."""
+    if params.fft_path not in (1, 3):
+        return []
+    dims = np.asarray(dims, np.int64)
+    Ls = sorted({math.lcm(*[int(v) for v in d]) for d in dims})
+    base = [fft_stages(L, 0) for L in Ls]
+    out = []
+    for rp in (1, 2, 3):
+        if any(fft_stages(L, rp) != b for L, b in zip(Ls, base)):
+            out.append(replace(params, radix_plan=rp))
+    return out
+
+
 def _time(plan, args, reps, flush):
     """Mean launch time over at least `reps` launches; short launches get more of them (about 4 ms
     of timed work, at most 50), so that candidates a few microseconds apart are told apart."""
@@ -100,23 +130,32 @@ def tune(dims, params: Params, cubes, offsets, alpha, tau, reps=5, cache_path=DE
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=cubes.device)
     timings = {}
     best, best_ms = None, float("inf")
-    for cand in candidates(dims, params):
-        try:
-            plan = Plan(dims, cand)
-        except FpssftError as e:
-            if e.status == ERR_UNSUPPORTED:
-                continue
-            raise
-        out = plan.alloc_output(cubes.device)
-        ms = _time(plan, (cubes, offsets, alpha, tau, out), reps, flush)
-        desc = f"path={cand.fft_path} gather={cand.gather_mode} threads={plan.info['threads']}"
-        timings[desc] = ms
-        if ms < best_ms:
-            best, best_ms = cand, ms
-        plan.close()
+
+    def run(cands):
+        nonlocal best, best_ms
+        for cand in cands:
+            try:
+                plan = Plan(dims, cand)
+            except FpssftError as e:
+                if e.status == ERR_UNSUPPORTED:
+                    continue
+                raise
+            out = plan.alloc_output(cubes.device)
+            ms = _time(plan, (cubes, offsets, alpha, tau, out), reps, flush)
+            desc = f"path={cand.fft_path} gather={cand.gather_mode} threads={plan.info['threads']}"
+            if cand.radix_plan:
+                desc += f" radix_plan={cand.radix_plan}"
+            timings[desc] = ms
+            if ms < best_ms:
+                best, best_ms = cand, ms
+            plan.close()
+
+    run(candidates(dims, params))
     if best is None:
         return params, timings
-    choice = {"fft_path": best.fft_path, "gather_mode": best.gather_mode, "threads": best.threads}
+    run(radix_candidates(dims, best))
+    choice = {"fft_path": best.fft_path, "gather_mode": best.gather_mode, "threads": best.threads,
+              "radix_plan": best.radix_plan}
     if cache_path:
         cache[key] = {"choice": choice, "timings": timings}
         try:

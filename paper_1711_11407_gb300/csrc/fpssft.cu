@@ -184,18 +184,39 @@ FastDiv make_fastdiv(int d) {
   return f;
 }
 
-std::vector<int> factorize(int L) {
-  std::vector<int> r;
-  int n = L;
-  while (n % 8 == 0) { r.push_back(8); n /= 8; }
-  while (n % 4 == 0) { r.push_back(4); n /= 4; }
-  while (n % 2 == 0) { r.push_back(2); n /= 2; }
-  while (n % 3 == 0) { r.push_back(3); n /= 3; }
-  while (n % 5 == 0) { r.push_back(5); n /= 5; }
-  for (int f = 7; (long long)f * f <= n; f += 2) {
-    while (n % f == 0) { r.push_back(f); n /= f; }
+// Mixed-radix stage sequence of an L-point FFT under a radix plan (fpssft_params.radix_plan):
+// every plan multiplies out to L; only the order and the split of the power of two differ.
+std::vector<int> factorize(int L, int plan) {
+  int n = L, e = 0;
+  while (n % 2 == 0) { n /= 2; ++e; }
+  std::vector<int> two, odd;
+  if (plan == 1) {
+    for (; e >= 2; e -= 2) two.push_back(4);
+    if (e == 1) two.push_back(2);
+  } else if (plan == 3) {
+    const int fours = e == 1 ? 0 : (e % 3 == 1 ? 2 : (e % 3 == 2 ? 1 : 0));
+    for (int q = 0; q < (e - 2 * fours) / 3; ++q) two.push_back(8);
+    for (int q = 0; q < fours; ++q) two.push_back(4);
+    if (e == 1) two.push_back(2);
+  } else {
+    for (; e >= 3; e -= 3) two.push_back(8);
+    if (e == 2) two.push_back(4);
+    if (e == 1) two.push_back(2);
   }
-  if (n > 1) r.push_back(n);
+  while (n % 3 == 0) { odd.push_back(3); n /= 3; }
+  while (n % 5 == 0) { odd.push_back(5); n /= 5; }
+  for (int f = 7; (long long)f * f <= n; f += 2) {
+    while (n % f == 0) { odd.push_back(f); n /= f; }
+  }
+  if (n > 1) odd.push_back(n);
+  std::vector<int> r;
+  if (plan == 2) {
+    r = odd;
+    r.insert(r.end(), two.begin(), two.end());
+  } else {
+    r = two;
+    r.insert(r.end(), odd.begin(), odd.end());
+  }
   return r;
 }
 
@@ -249,6 +270,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
   if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
   if (pr.fft_path < 0 || pr.fft_path > 3) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 3]");
+  if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
   if (pr.threads < 0 || pr.threads > 1024 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 1024]");
 
   auto* P = new (std::nothrow) fpssft_plan_s();
@@ -289,7 +311,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       int stride = 1;
       for (int d = D - 1; d >= 0; --d) { sh.dims[d] = dv[d]; sh.strides[d] = stride; stride *= dv[d]; }
       for (int d = 0; d < D; ++d) sh.c[d] = (int)(L / dv[d]);
-      auto rad = factorize((int)L);
+      auto rad = factorize((int)L, pr.radix_plan);
       if ((int)rad.size() > kMaxStages) { delete P; return fail(FPSSFT_ERR_UNSUPPORTED, "too many FFT stages"); }
       sh.nst = (int)rad.size();
       for (int d = 0; d < kMaxD; ++d) sh.fdims[d] = make_fastdiv(d < D ? dv[d] : 1);
@@ -1101,6 +1123,17 @@ extern "C" fpssft_status fpssft_l2_fetch_granularity(int bytes, int* previous) {
   return FPSSFT_OK;
 }
 
+extern "C" fpssft_status fpssft_fft_stages(int L, int radix_plan, int32_t* radices, int32_t* n_stages) {
+  if (!radices || !n_stages) return fail(FPSSFT_ERR_INVALID, "null output");
+  if (L < 1 || L > (1 << 24)) return fail(FPSSFT_ERR_INVALID, "L must be in [1, 2^24]");
+  if (radix_plan < 0 || radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
+  const std::vector<int> r = factorize(L, radix_plan);
+  if ((int)r.size() > kMaxStages) return fail(FPSSFT_ERR_UNSUPPORTED, "too many FFT stages");
+  for (size_t i = 0; i < r.size(); ++i) radices[i] = r[i];
+  *n_stages = (int32_t)r.size();
+  return FPSSFT_OK;
+}
+
 extern "C" const char* fpssft_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* fpssft_version(void) { return "fpssft-gb300 0.1 (sm_103a)"; }
@@ -1169,18 +1202,11 @@ __global__ void __launch_bounds__(256) k_noalloc_upload(const __grid_constant__ 
   for (int i = threadIdx.x; i < c.n16; i += blockDim.x) c.dst[i] = c.data[i];
 }
 
-int factorize_into(int L, int* out) {
-  int n = L, k = 0;
-  const int small[] = {8, 4, 2, 3, 5};
-  for (int f : small)
-    while (n % f == 0 && k < kMaxStages) { out[k++] = f; n /= f; }
-  for (int f = 7; (long long)f * f <= n && k < kMaxStages; f += 2)
-    while (n % f == 0 && k < kMaxStages) { out[k++] = f; n /= f; }
-  if (n > 1) {
-    if (k >= kMaxStages) return -1;
-    out[k++] = n;
-  }
-  return k;
+int factorize_into(int L, int plan, int* out) {
+  const std::vector<int> r = factorize(L, plan);
+  if ((int)r.size() > kMaxStages) return -1;
+  for (size_t s = 0; s < r.size(); ++s) out[s] = r[s];
+  return (int)r.size();
 }
 
 }  // namespace
@@ -1203,6 +1229,7 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
   if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
   if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
+  if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
 
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   int dev = 0;
@@ -1262,7 +1289,7 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
       int stride = 1;
       for (int d = D - 1; d >= 0; --d) { sh.dims[d] = dv[d]; sh.strides[d] = stride; stride *= dv[d]; }
       for (int d = 0; d < D; ++d) sh.c[d] = (int)(L / dv[d]);
-      const int nst = factorize_into((int)L, sh.radix);
+      const int nst = factorize_into((int)L, pr.radix_plan, sh.radix);
       if (nst < 0) return fail(FPSSFT_ERR_UNSUPPORTED, "too many FFT stages");
       sh.nst = nst;
       for (int d = 0; d < kMaxD; ++d) sh.fdims[d] = make_fastdiv(d < D ? dv[d] : 1);

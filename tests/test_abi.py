@@ -32,7 +32,8 @@ def test_library_exports_every_declared_function():
 def _plan(D, batch, dims, **kw):
     lib = _lib.load()
     p = _lib.CParams(kw.get("T", 10), kw.get("k_cap", 64), kw.get("theta0", 1e-3), 1e-3, 0.05, 1,
-                     kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0), kw.get("fft_path", 0), 0)
+                     kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0), kw.get("fft_path", 0), 0,
+                     kw.get("radix_plan", 0))
     h = ctypes.c_void_p()
     d = np.ascontiguousarray(np.asarray(dims, np.int64).reshape(-1))
     st = lib.fpssft_plan_create(ctypes.byref(h), D, batch, d.ctypes.data_as(ctypes.c_void_p) if d.size else None,
@@ -53,6 +54,8 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
     (2, 1, [8, 8], {"gather_mode": 4}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"fft_path": 4}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"radix_plan": -1}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"radix_plan": 4}, _lib.ERR_INVALID),
     (2, 1, [1 << 20, 3], {}, _lib.ERR_UNSUPPORTED),         # D L max N_d >= 2^31
     (2, 1, [65536, 65536], {}, _lib.ERR_UNSUPPORTED),       # N >= 2^31
 ])
@@ -116,3 +119,36 @@ def test_a_missing_library_fails_loudly_instead_of_falling_back(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == f"raised {_lib.ERR_UNSUPPORTED}"
+
+
+@pytest.mark.parametrize("plan", [0, 1, 2, 3])
+def test_fft_stage_sequences_multiply_to_L_in_the_plan_order(plan):
+    """fpssft_fft_stages (host only): every radix plan is a factorisation of L; plan 1 has no
+    radix 8, plan 2 puts the odd factors first, plan 3 has no radix 2 unless L's power of two is 2,
+    plan 0 has at most one radix-4 or radix-2 stage."""
+    lib = _lib.load()
+    out = (ctypes.c_int32 * 24)()
+    n = ctypes.c_int32(0)
+    for L in [1, 2, 3, 4, 7, 12, 64, 96, 128, 240, 256, 360, 512, 576, 1024, 2048, 3840, 4608, 7919, 2 * 7919,
+              (1 << 23) * 2]:
+        if L > (1 << 24):
+            assert lib.fpssft_fft_stages(L, plan, out, ctypes.byref(n)) == _lib.ERR_INVALID
+            continue
+        assert lib.fpssft_fft_stages(L, plan, out, ctypes.byref(n)) == _lib.OK
+        r = [out[i] for i in range(n.value)]
+        assert int(np.prod(r, dtype=np.int64)) == L, (L, plan, r)
+        e = (L & -L).bit_length() - 1
+        twos = [v for v in r if v in (2, 4, 8)]
+        odd = [v for v in r if v not in (2, 4, 8)]
+        assert odd == sorted(odd)
+        if plan == 1:
+            assert 8 not in r
+        if plan == 2:
+            assert r == odd + twos
+        else:
+            assert r == twos + odd
+        if plan == 3 and e >= 2:
+            assert 2 not in r
+        if plan == 0:
+            assert sum(v in (2, 4) for v in r) <= 1
+    assert lib.fpssft_fft_stages(64, 5, out, ctypes.byref(n)) == _lib.ERR_INVALID

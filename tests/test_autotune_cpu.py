@@ -46,3 +46,20 @@ def test_cache_hit_returns_the_stored_choice_without_timing(tmp_path, monkeypatc
                                   cache_path=str(path))
     assert (best.fft_path, best.gather_mode, best.threads, best.k_cap) == (2, 1, 96, 512)
     assert timings == stored["timings"]
+
+
+def test_radix_plan_candidates_only_where_the_stage_sequence_changes():
+    """Radix plans are offered for the shared-memory FFT paths, and only those whose stage sequence
+    differs from the default for some line length of the batch (3840 = 8 8 4 3 5 by default)."""
+    from dataclasses import replace
+    p = Params(T=0, k_cap=640)
+    dims = np.array([[240, 256]])
+    assert autotune.radix_candidates(dims, replace(p, fft_path=2)) == []
+    c = autotune.radix_candidates(dims, replace(p, fft_path=3, threads=512))
+    assert {x.radix_plan for x in c} == {1, 2}          # plan 3 gives 8 8 4 3 5 as well
+    assert all(x.fft_path == 3 and x.threads == 512 for x in c)
+    assert autotune.fft_stages(3840, 1) == [4, 4, 4, 4, 3, 5]
+    assert autotune.fft_stages(3840, 2) == [3, 5, 8, 8, 4]
+    c = autotune.radix_candidates(np.array([[1024, 1024]]), replace(p, fft_path=3))   # 1024 = 8 8 8 2
+    assert {x.radix_plan for x in c} == {1, 3}
+    assert autotune.fft_stages(1024, 3) == [8, 8, 4, 4]

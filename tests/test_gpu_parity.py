@@ -388,14 +388,19 @@ def test_register_fft_path_equals_shared_memory_path(case):
         assert_same_set(k, aa, ref, f"signal {i}")
 
 
-def test_autotuned_launch_computes_the_same_sets():
+@pytest.mark.parametrize("name,batch", [("uneven_2d", 256), ("single_240x256", None), ("sparse_image_512x576", 2)])
+def test_autotuned_launch_computes_the_same_sets(name, batch):
+    """The tuned launch (kernel path, gather, CTA size and, for the long lines, the FFT's radix plan)
+    recovers what the default launch recovers."""
     from paper_1711_11407_gb300 import autotune
     from paper_1711_11407_gb300.api import Plan
-    wl = S.make_workload("uneven_2d", batch=256)
+    wl = S.make_workload(name, batch=batch)
     p = configs.params_for(wl)
     t = to_dev(wl)
     best, timings = autotune.tune(wl.dims, p, *t, reps=2, cache_path=None)
     assert len(timings) >= 2
+    if name != "uneven_2d":
+        assert any("radix_plan" in d for d in timings), f"no radix plan was timed: {sorted(timings)}"
     ref = Plan(wl.dims, p).recover(*t)
     got = Plan(wl.dims, best).recover(*t)
     torch.cuda.synchronize()
@@ -403,6 +408,33 @@ def test_autotuned_launch_computes_the_same_sets():
     for b in range(wl.batch):
         n = int(ref.count[b])
         assert torch.equal(ref.k[b, :n], got.k[b, :n])
+        assert torch.allclose(ref.a[b, :n], got.a[b, :n], rtol=AMP_TOL, atol=0)
+
+
+@pytest.mark.parametrize("radix_plan", [1, 2, 3])
+@pytest.mark.parametrize("fft_path", [1, 3])
+def test_every_radix_plan_matches_the_oracle(radix_plan, fft_path):
+    """Each radix plan of the shared-memory FFT (stage orders and radix splits of L = 3840, 1440,
+    1024 and 360) gives the oracle's line DFTs and recovered sets."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = small_batch([(240, 256), (96, 120), (32, 1024), (40, 72)], 4, K=lambda N: 24, T=8, seed=17, snr_db=None)
+    p = configs.params_for(wl, T=8, k_cap=64, fft_path=fft_path, radix_plan=radix_plan)
+    plan = Plan(wl.dims, p)
+    t = to_dev(wl)
+    out = plan.recover(*t)
+    bins = plan.project(t[0], t[1], t[2][:, :2].contiguous(), t[3][:, :2].contiguous()).cpu().numpy()
+    torch.cuda.synchronize()
+    for b in range(wl.batch):
+        L = int(plan.L[b])
+        for s in range(2):
+            ref = O.project(wl.cube(b), wl.alpha[b, s], wl.tau[b, s])
+            for j in range(wl.D + 1):
+                e = np.linalg.norm(bins[b, s, j, :L] - ref[j]) / np.linalg.norm(ref[j])
+                assert e <= BIN_TOL, f"radix plan {radix_plan}: line bins rel L2 {e:.2e}, dims {wl.dims[b]}"
+        ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, 8))
+        k, a = out.signal(b)
+        assert_same_set(k, a, ref, f"radix plan {radix_plan} path {fft_path} dims {wl.dims[b]}")
+        assert int(out.iters[b]) == ref.iters
 
 
 def test_1024_thread_cta_equals_512_thread_cta_and_oracle():
