@@ -607,62 +607,51 @@ def main():
 
     if not args.quick:
         # ---- end to end through the host-buffer call ------------------------------------------
+        # fpssft_recover_host in both host modes: every cube copied to the device (host_cubes 0), or
+        # pinned cubes read in place over the host link, only offsets, schedules and results
+        # copied (host_cubes 1).  Both are timed; `e2e` is the faster one, both are reported.
+        from dataclasses import replace as _replace
+
+        from paper_1711_11407_gb300.api import Plan as _Plan
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_cubes, h_offs, h_alpha, h_tau = pin(wl.cubes), pin(wl.offsets), pin(wl.alpha), pin(wl.tau)
-        h_out = plan.alloc_output("cpu")
-        for f in ("k", "a", "count", "iters", "status"):
-            setattr(h_out, f, getattr(h_out, f).pin_memory())
-        with torch.cuda.stream(stream):
-            plan.recover_host(h_cubes, h_offs, h_alpha, h_tau, out=h_out, stream=stream)
-            if world > 1:
-                dist.barrier()
-            e2e_ms = []
-            for _ in range(args.steps):
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                plan.recover_host(h_cubes, h_offs, h_alpha, h_tau, out=h_out, stream=stream)
-                a1.record(stream)
-                a1.synchronize()
-                e2e_ms.append(a0.elapsed_time(a1))
-        same = same_sets(out, h_out)        # the last fpssft_recover_host run against the timed device run
-        # end to end with the cubes left in pinned host memory (read in place over the host link):
-        # per step the offsets and schedule are copied in and the outputs copied out
-        d_offs, d_alpha, d_tau = torch.empty_like(offs), torch.empty_like(alpha), torch.empty_like(tau)
-        m_out = plan.alloc_output(dev)
-        hm_out = plan.alloc_output("cpu")
-        for f in ("k", "a", "count", "iters", "status"):
-            setattr(hm_out, f, getattr(hm_out, f).pin_memory())
-        with torch.cuda.stream(stream):
-            def mapped_step():
-                d_offs.copy_(h_offs, non_blocking=True)
-                d_alpha.copy_(h_alpha, non_blocking=True)
-                d_tau.copy_(h_tau, non_blocking=True)
-                plan.recover_mapped(h_cubes, d_offs, d_alpha, d_tau, out=m_out, stream=stream)
-                for f in ("k", "a", "count", "iters", "status"):
-                    getattr(hm_out, f).copy_(getattr(m_out, f), non_blocking=True)
-            mapped_step()
-            stream.synchronize()
-            map_ms = []
-            for _ in range(args.steps):
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                mapped_step()
-                a1.record(stream)
-                a1.synchronize()
-                map_ms.append(a0.elapsed_time(a1))
-        mapped_same = same_sets(out, hm_out)
-        e2e_step = max_over_ranks(sum(e2e_ms), world, dev) / args.steps
-        h2d = sum(int(x.numel() * x.element_size()) for x in (h_cubes, h_offs, h_alpha, h_tau))
-        d2h = sum(int(getattr(h_out, f).numel() * getattr(h_out, f).element_size()) for f in ("k", "a", "count", "iters", "status"))
-        line["e2e"] = {"value": job_rate(wl.batch, world, e2e_step), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step, "call": "fpssft_recover_host",
-                       "matches_device_run": same}
-        map_step = max_over_ranks(sum(map_ms), world, dev) / args.steps
         small = sum(int(x.numel() * x.element_size()) for x in (h_offs, h_alpha, h_tau))
-        line["e2e_host_mapped"] = {"value": job_rate(wl.batch, world, map_step), "unit": UNIT,
-                                   "h2d_bytes_per_step": small, "d2h_bytes_per_step": d2h, "ms_per_step": map_step,
-                                   "call": "fpssft_recover with the cubes in pinned host memory (read in place)",
-                                   "cube_bytes_read_in_place_algorithmic": useful, "matches_device_run": mapped_same}
+        modes = {}
+        for hc in (0, 1):
+            hplan = _Plan(wl.dims, _replace(p, host_cubes=hc))
+            h_out = hplan.alloc_output("cpu")
+            for f in ("k", "a", "count", "iters", "status"):
+                setattr(h_out, f, getattr(h_out, f).pin_memory())
+            with torch.cuda.stream(stream):
+                hplan.recover_host(h_cubes, h_offs, h_alpha, h_tau, out=h_out, stream=stream)
+                if world > 1:
+                    dist.barrier()
+                e2e_ms = []
+                for _ in range(args.steps):
+                    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    hplan.recover_host(h_cubes, h_offs, h_alpha, h_tau, out=h_out, stream=stream)
+                    a1.record(stream)
+                    a1.synchronize()
+                    e2e_ms.append(a0.elapsed_time(a1))
+            e2e_step = max_over_ranks(sum(e2e_ms), world, dev) / args.steps
+            d2h = sum(int(getattr(h_out, f).numel() * getattr(h_out, f).element_size())
+                      for f in ("k", "a", "count", "iters", "status"))
+            rec = {"value": job_rate(wl.batch, world, e2e_step), "unit": UNIT, "ms_per_step": e2e_step,
+                   "h2d_bytes_per_step": small + (h_cubes.numel() * h_cubes.element_size() if hc == 0 else 0),
+                   "d2h_bytes_per_step": d2h, "call": "fpssft_recover_host", "host_cubes": hc,
+                   # the last run of this mode against the timed device run: whole sets compared
+                   "matches_device_run": same_sets(out, h_out)}
+            if hc == 1:
+                rec["h2d_bytes_read_in_place_algorithmic"] = useful
+                rec["note"] = ("pinned cubes read in place over NVLink-C2C: the gather fetches only the samples "
+                               "the iterations use; h2d_bytes_per_step counts the copied offsets and schedules")
+            modes["copy" if hc == 0 else "in_place"] = rec
+            hplan.close()
+        best = min(modes.values(), key=lambda r: r["ms_per_step"])
+        line["e2e"] = dict(best)
+        line["e2e_modes"] = {k: {kk: v[kk] for kk in ("value", "ms_per_step", "h2d_bytes_per_step", "matches_device_run")}
+                             for k, v in modes.items()}
 
         # ---- plain per-signal GPU form on a sample ---------------------------------------------
         from paper_1711_11407_gb300._lib import ERR_UNSUPPORTED, FpssftError

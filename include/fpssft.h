@@ -101,6 +101,13 @@ typedef struct {
                         2 = the odd factors (3, 5, larger primes) first, then 8, 4, 2;
                         3 = the power of two as radix 8 and 4 stages only (no radix-2 stage unless
                             L's power of two is 2), then the odd factors */
+  int host_cubes;    /* fpssft_recover_host only: 0 = copy every cube to the device before the
+                        recovery; 1 = when `cubes` is pinned host memory the device can address
+                        (cudaHostAlloc, cudaMallocHost or cudaHostRegister), read the samples the
+                        gather needs in place over the host link (NVLink-C2C on GB300) and copy only
+                        offsets, schedules and results -- FPS-SFT reads a fraction of each cube, so
+                        this moves far fewer bytes when the early stop comes soon; other host memory
+                        is copied as with 0 */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;
@@ -187,9 +194,10 @@ fpssft_status fpssft_recover(fpssft_plan_t plan, const void* cubes, const int64_
 
 /* fpssft_recover on HOST buffers: cubes (complex64, total elements = sum N_b), offsets, alpha,
  * tau and init_count in host memory (pinned memory gives full copy bandwidth).  The call copies
- * the inputs into plan-owned device staging (allocated on the first call), runs the recovery on
- * `stream`, copies every output back into the host arrays and synchronises the stream before
- * returning. */
+ * the inputs into plan-owned device staging (allocated on the first call that needs it; with
+ * fpssft_params.host_cubes = 1 pinned cubes are read in place instead of copied), runs the
+ * recovery on `stream`, copies every output back into the host arrays and synchronises the stream
+ * before returning. */
 fpssft_status fpssft_recover_host(fpssft_plan_t plan, const void* cubes, const int64_t* offsets,
                                   const int32_t* alpha, const int32_t* tau, const int32_t* init_count,
                                   int32_t* out_k, void* out_a, int32_t* out_count, int32_t* out_iters,

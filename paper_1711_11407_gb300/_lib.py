@@ -85,7 +85,8 @@ class CParams(ctypes.Structure):
                 ("eta", ctypes.c_float), ("early_stop", ctypes.c_int), ("peel_mode", ctypes.c_int),
                 ("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("fp64_decisions", ctypes.c_int), ("gather_mode", ctypes.c_int), ("fft_path", ctypes.c_int),
-                ("amp_average", ctypes.c_int), ("radix_plan", ctypes.c_int)]
+                ("amp_average", ctypes.c_int), ("radix_plan", ctypes.c_int),
+                ("host_cubes", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

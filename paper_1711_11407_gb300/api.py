@@ -31,12 +31,13 @@ class Params:
     fft_path: int = 0
     amp_average: bool = False
     radix_plan: int = 0
+    host_cubes: int = 0
 
     def c(self):
         return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
                             int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
                             int(bool(self.fp64_decisions)), int(self.gather_mode), int(self.fft_path),
-                            int(bool(self.amp_average)), int(self.radix_plan))
+                            int(bool(self.amp_average)), int(self.radix_plan), int(self.host_cubes))
 
 
 @dataclass

@@ -271,6 +271,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
   if (pr.fft_path < 0 || pr.fft_path > 3) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 3]");
   if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
+  if (pr.host_cubes < 0 || pr.host_cubes > 1) return fail(FPSSFT_ERR_INVALID, "host_cubes must be 0 or 1");
   if (pr.threads < 0 || pr.threads > 1024 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 1024]");
 
   auto* P = new (std::nothrow) fpssft_plan_s();
@@ -767,19 +768,27 @@ extern "C" fpssft_status fpssft_recover_host(fpssft_plan_t P, const void* cubes,
   }
   const size_t sched = B * (size_t)P->T_max * D;
   auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, std::max<size_t>(bytes, 16)); };
-  if (P->st_cubes != nullptr && elems > P->st_cubes_elems) {
+  // cubes in pinned host memory the device can address are read in place when the plan asks for it
+  const void* in_place = nullptr;
+  if (P->p.host_cubes == 1) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, cubes) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr)
+      in_place = at.devicePointer;
+    cudaGetLastError();   // a pointer the runtime does not know is pageable memory: copy it
+  }
+  if (!in_place && P->st_cubes != nullptr && elems > P->st_cubes_elems) {
     cudaFree(P->st_cubes);
     P->st_cubes = nullptr;
     P->st_cubes_elems = 0;
-    if (alloc(&P->st_cubes, elems * sizeof(float2)) != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, "staging allocation failed");
-    P->st_cubes_elems = elems;
+  }
+  if (!in_place && P->st_cubes == nullptr) {
+    const size_t n = std::max(elems, P->total_elems);
+    if (alloc(&P->st_cubes, n * sizeof(float2)) != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, "staging allocation failed");
+    P->st_cubes_elems = n;
   }
   if (P->st_offsets == nullptr) {
     cudaError_t e = cudaSuccess;
-    if (P->st_cubes == nullptr) {
-      e = alloc(&P->st_cubes, std::max(elems, P->total_elems) * sizeof(float2));
-      P->st_cubes_elems = std::max(elems, P->total_elems);
-    }
     if (e == cudaSuccess) e = alloc((void**)&P->st_offsets, B * sizeof(int64_t));
     if (e == cudaSuccess) e = alloc((void**)&P->st_alpha, sched * sizeof(int32_t));
     if (e == cudaSuccess) e = alloc((void**)&P->st_tau, sched * sizeof(int32_t));
@@ -791,7 +800,8 @@ extern "C" fpssft_status fpssft_recover_host(fpssft_plan_t P, const void* cubes,
     if (e == cudaSuccess) e = alloc((void**)&P->st_status, B * sizeof(int32_t));
     if (e != cudaSuccess) return fail(FPSSFT_ERR_ALLOC, std::string("staging allocation: ") + cudaGetErrorString(e));
   }
-  FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_cubes, cubes, elems * sizeof(float2), cudaMemcpyHostToDevice, s));
+  if (!in_place)
+    FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_cubes, cubes, elems * sizeof(float2), cudaMemcpyHostToDevice, s));
   FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_offsets, offsets, B * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_alpha, alpha, sched * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_tau, tau, sched * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -802,8 +812,8 @@ extern "C" fpssft_status fpssft_recover_host(fpssft_plan_t P, const void* cubes,
     FPSSFT_CUDA_TRY(cudaMemcpyAsync(P->st_a, out_a, B * kc * sizeof(float2), cudaMemcpyHostToDevice, s));
     dinit = P->st_init;
   }
-  fpssft_status st = fpssft_recover(P, P->st_cubes, P->st_offsets, P->st_alpha, P->st_tau, dinit, P->st_k, P->st_a,
-                                    P->st_count, P->st_iters, P->st_status, stream);
+  fpssft_status st = fpssft_recover(P, in_place ? in_place : P->st_cubes, P->st_offsets, P->st_alpha, P->st_tau, dinit,
+                                    P->st_k, P->st_a, P->st_count, P->st_iters, P->st_status, stream);
   if (st != FPSSFT_OK) return st;
   FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_k, P->st_k, B * kc * D * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   FPSSFT_CUDA_TRY(cudaMemcpyAsync(out_a, P->st_a, B * kc * sizeof(float2), cudaMemcpyDeviceToHost, s));

@@ -298,6 +298,29 @@ def test_recover_host_buffers_equal_device_buffers():
             assert torch.allclose(hv.a[b, :n], dv.a[b, :n].cpu(), rtol=AMP_TOL, atol=0)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_recover_host_reading_pinned_cubes_in_place_equals_device_buffers(pinned):
+    """host_cubes = 1: pinned cubes are read in place over the host link (nothing of them copied);
+    pageable cubes are copied as before.  Either way the sets equal the device run's, on two calls
+    in a row (the second reuses the plan's staging)."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=64)
+    p = configs.params_for(wl, host_cubes=1)
+    plan = Plan(wl.dims, p)
+    dv = plan.recover(*to_dev(wl))
+    torch.cuda.synchronize()
+    cubes = torch.from_numpy(wl.cubes)
+    if pinned:
+        cubes = cubes.pin_memory()
+    for _ in range(2):
+        hv = plan.recover_host(cubes, wl.offsets, wl.alpha, wl.tau)
+        assert torch.equal(hv.count, dv.count.cpu()) and torch.equal(hv.iters, dv.iters.cpu())
+        for b in range(wl.batch):
+            n = int(hv.count[b])
+            assert torch.equal(hv.k[b, :n], dv.k[b, :n].cpu())
+            assert torch.allclose(hv.a[b, :n], dv.a[b, :n].cpu(), rtol=AMP_TOL, atol=0)
+
+
 def test_empty_batch_is_a_no_op():
     from paper_1711_11407_gb300.api import Plan
     plan = Plan(np.zeros((0, 2), np.int64))
