@@ -22,7 +22,9 @@ Readings of points the paper leaves open (each one is stated where it is used):
     the literal IDFT-subtract-DFT order is kept as `peel_mode="literal"`;
   * a frequency decoded again accumulates its amplitude; entries with |a| <= theta0 are dropped at
     output; the output is sorted by linear frequency index;
-  * optional early stop when no bin of line 0 passes T0 after peeling;
+  * optional early stop (the paper runs T iterations): either when no bin of line 0 passes T0
+    after peeling (the iteration that finds nothing is counted), or already after an iteration in
+    which every line-0 bin passing T0 was decoded (what was left on the line is now recovered);
   * optional amplitude averaged over the D+1 phase-corrected lines (`decoded_amplitude`);
   * a full set (k_cap entries) drops new frequencies, flags the signal and stops it.
 
@@ -52,7 +54,9 @@ class Params:
     theta0: float = 1e-3        # T0: |s_0(m)| > theta0
     rho: float = 1e-3           # T1: ||s_{d+1}(m)| - |s_0(m)|| <= rho |s_0(m)|
     eta: float = 0.05           # T2: |N_d phi / (2 pi) - round| <= eta
-    early_stop: bool = True     # stop when no bin of line 0 passes T0 after peeling
+    early_stop: int = 1         # 0: run T iterations; 1: stop when no bin of line 0 passes T0 after
+                                # peeling; 2: also stop after an iteration whose line-0 bins passing
+                                # T0 were all decoded
     peel_mode: str = "bins"     # "bins" (subtract projections from the bins) or "literal"
     amp_average: bool = False   # amplitude from line tau only (Eq. decoding) or averaged over the D+1 lines
 
@@ -335,6 +339,8 @@ def recover(x, alpha, tau, p, init=None, T=None, keep_history=False):
         hist.append((len(S), n_t0))
         if status != STATUS_OK:
             break
+        if p.early_stop == 2 and len(cands) == n_t0:
+            break           # every bin with energy left on line 0 was one frequency, now recovered
     keep = [(kk, aa) for kk, aa in S.items() if abs(aa) > p.theta0]
     k = np.asarray([kk for kk, _ in keep], np.int64).reshape(-1, D)
     a = np.asarray([aa for _, aa in keep], np.complex128)
@@ -510,6 +516,8 @@ def recover_offset_sets(x, alpha, taus, p):
             break
         if not merge(S, cands, p.k_cap):
             status = STATUS_CAPACITY
+            break
+        if p.early_stop == 2 and len(cands) == n_t0:
             break
     keep = [(kk, aa) for kk, aa in S.items() if abs(aa) > p.theta0]
     k = np.asarray([kk for kk, _ in keep], np.int64).reshape(-1, D)

@@ -276,6 +276,39 @@ def check_early_stop(O):
     assert full.history[-1][1] == 0, "the last iteration found no bin passing T0"
 
 
+def check_early_stop_decoded(O):
+    """The second stop reading (early_stop = 2): a run stops after an iteration in which every
+    line-0 bin passing T0 was decoded.  (1) Noiseless: it ends in the very iteration that completed
+    the set, one before the first reading, with the same set.  (2) With many frequencies per bin,
+    iterations that leave undecoded energy do not stop it: over seeds where bins collide it still
+    returns the planted spectrum.  (3) Tiny cubes: the support equals the dense DFT's."""
+    dims, T = (16, 24), 40
+    for seed in (6, 7, 8):
+        k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence(seed), dims, 10, T)
+        r1 = O.recover(x, al, ta, O.Params(T=T, k_cap=64, early_stop=1), keep_history=True)
+        r2 = O.recover(x, al, ta, O.Params(T=T, k_cap=64, early_stop=2))
+        sizes = [h[0] for h in r1.history]
+        done = sizes.index(len(k)) + 1
+        assert r2.iters == done == r1.iters - 1, "the decoded-stop ends in the iteration that completes the set"
+        assert np.array_equal(r2.k, r1.k) and np.allclose(r2.a, r1.a, atol=1e-12)
+    for seed in range(10, 16):
+        k, a, x, _, al, ta = S.make_signal(np.random.SeedSequence(seed), dims, 40, T)   # 40 / 48 per bin
+        r2 = O.recover(x, al, ta, O.Params(T=T, k_cap=128, early_stop=2), keep_history=True)
+        assert np.array_equal(O.linear_index(r2.k, dims), np.sort(O.linear_index(k, dims))), \
+            f"seed {seed}: stopped before the set was complete"
+        assert any(h[1] > 0 for h in r2.history[:-1]) or r2.iters == 1
+    rng = np.random.default_rng(3)
+    for dims in [(8, 8), (12, 18), (8, 8, 8)]:
+        N = int(np.prod(dims))
+        k = grid(dims)[rng.choice(N, 5, replace=False)]
+        a = np.exp(2j * np.pi * rng.random(5))
+        x = S.synthesize_cube(dims, k, a)
+        al, ta = S.draw_schedule(rng, dims, 60)
+        r = O.recover(x, al, ta, O.Params(T=60, k_cap=32, early_stop=2))
+        dense = O.dense_dft(x)
+        assert np.array_equal(O.linear_index(r.k, dims), np.sort(np.nonzero(np.abs(dense.reshape(-1)) > 1e-3)[0]))
+
+
 # --- capacity: a full set drops new frequencies, flags the signal and stops it -------------------
 
 def check_capacity(O):

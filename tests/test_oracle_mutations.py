@@ -33,6 +33,7 @@ CHECKS = [
     pins.check_amplitude_average,
     pins.check_refine_lstsq,
     pins.check_offset_sets,
+    pins.check_early_stop_decoded,
 ]
 
 _orig = {name: getattr(O, name) for name in dir(O) if callable(getattr(O, name))}
@@ -211,6 +212,13 @@ def _sets_amplitude_from_first(bins_s, alpha, taus, dims, p):
     return [(m, k, O.decoded_amplitude(bins_s[0], m, k, taus[0], dims, p.amp_average)) for m, k, _ in cands], n0
 
 
+def _classify_claims_every_bin_decoded(bins, alpha, tau, dims, p):
+    # the decoded-stop fires after any iteration that decoded something (T0 count replaced by the
+    # number of decodes whenever there is one)
+    cands, n0 = _orig["classify_decode"](bins, alpha, tau, dims, p)
+    return cands, (len(cands) if cands else n0)
+
+
 MUTATIONS = {
     "dft sign flipped": ("line_dft", _dft_plus_sign),
     "dft 1/L dropped": ("line_dft", _dft_no_scale),
@@ -238,6 +246,7 @@ MUTATIONS = {
     "least squares replaced by the mean of the decodes": ("refine_lstsq", _refine_mean_of_decodes),
     "offset sets: phase from the first set only": ("classify_decode_sets", _sets_phase_from_first),
     "offset sets: amplitude from the first set only": ("classify_decode_sets", _sets_amplitude_from_first),
+    "decoded-stop fires after any decode": ("classify_decode", _classify_claims_every_bin_decoded),
 }
 
 

@@ -161,3 +161,7 @@ def test_least_squares_amplitudes_exact_noiseless_closed_form_and_normal_equatio
 
 def test_offset_sets_reduce_to_the_plain_loop_decode_exactly_and_average_the_noise():
     pins.check_offset_sets(O)
+
+
+def test_decoded_stop_ends_when_the_set_completes_and_never_early():
+    pins.check_early_stop_decoded(O)
