@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--gather-mode", type=int, default=0)
     ap.add_argument("--fft-path", type=int, default=0)
+    ap.add_argument("--early-stop", type=int, default=None,
+                    help="stop rule (0 none, 1 after an iteration with no line-0 bin passing T0, 2 also after "
+                         "an iteration whose line-0 bins passing T0 were all decoded); default: the workload's")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch configuration")
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1: leave)")
     ap.add_argument("--refine-rows", type=int, default=0,
@@ -286,7 +289,7 @@ class OraclePool:
         self.shm = shared_memory.SharedMemory(create=True, size=max(8, wl.cubes.nbytes))
         np.ndarray(wl.cubes.shape, np.complex64, buffer=self.shm.buf)[:] = wl.cubes
         pd = dict(T=int(params.T), k_cap=int(params.k_cap), theta0=float(params.theta0), rho=float(params.rho),
-                  eta=float(params.eta), early_stop=bool(params.early_stop))
+                  eta=float(params.eta), early_stop=int(params.early_stop))
         self.pool = mp.get_context("spawn").Pool(
             self.cores, initializer=_oracle_init,
             initargs=(self.shm.name, int(wl.cubes.size), wl.dims, wl.offsets, wl.alpha, wl.tau, wl.T, pd))
@@ -457,7 +460,8 @@ def main():
     if seed is None:
         seed = 1234 + {v: k for k, v in synth.WORKLOAD_IDS.items()}[args.workload] + 1000 * rank
     wl = synth.make_workload(args.workload, seed=seed, batch=args.batch)
-    p = configs.params_for(wl, threads=args.threads, ctas_per_sm=args.ctas_per_sm, gather_mode=args.gather_mode,
+    over = {} if args.early_stop is None else {"early_stop": args.early_stop}
+    p = configs.params_for(wl, **over, threads=args.threads, ctas_per_sm=args.ctas_per_sm, gather_mode=args.gather_mode,
                            fft_path=args.fft_path)
     from paper_1711_11407_gb300.api import l2_fetch_granularity
     l2_prev = l2_fetch_granularity(args.l2_fetch)

@@ -71,7 +71,13 @@ typedef struct {
   float theta0;      /* T0 threshold (absolute) */
   float rho;         /* T1 relative magnitude tolerance */
   float eta;         /* T2 distance of the decoded phase from the frequency grid */
-  int early_stop;    /* nonzero: stop a signal when no bin of line 0 passes T0 after peeling */
+  int early_stop;    /* 0: every signal runs its T iterations; 1 (any nonzero value but 2): stop a
+                        signal after an iteration in which no bin of line 0 passes T0 after
+                        peeling; 2: also stop it after an iteration in which every line-0 bin
+                        passing T0 was decoded (what was left on its lines is now recovered) --
+                        one iteration earlier on noiseless data (readings of the stop rule: the
+                        paper runs T iterations, Sec. 2.2, and counts the samples to perfect
+                        recovery, Sec. 3) */
   int peel_mode;     /* 0 = subtract the recovered set's projections from the bins (only mode) */
   int threads;       /* CTA size of the shared-memory-FFT recovery kernel (multiple of 32, <= 1024);
                         0 = library default */
@@ -84,7 +90,9 @@ typedef struct {
                         2 = synchronous cached in L2 only, 3 = asynchronous copies (cp.async) of the
                         next iteration's lines into a shared-memory buffer while the current one
                         computes.  On the register-FFT path modes 1 and 2 prefetch the next
-                        iteration into registers instead */
+                        iteration into registers instead; 4 = synchronous through L1 with no
+                        prefetch (on the register-FFT path the library's choice when the batch has
+                        more signals than resident CTAs; elsewhere the same as 1) */
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
                         FFT (every L of the batch in {32, 64, 128, 256}), 3 = one CTA per line, the
@@ -213,13 +221,15 @@ fpssft_status fpssft_synth(fpssft_plan_t plan, const int32_t* alpha, const int32
 
 /* One iteration's classification, decode and merge on precomputed bins [batch][1][D+1][L_max]
  * (already peeled), updating the set (k, a, count) in place, as in fpssft_recover.  Writes the
- * number of line-0 bins passing T0 to t0_count [batch] and ORs FPSSFT_ERR_CAPACITY into status.
+ * number of line-0 bins passing T0 to t0_count [batch], the number of bins decoded (T0..T3
+ * passed) to accepted [batch] (nullable; the two are equal when the decoded-stop of early_stop = 2
+ * applies) and ORs FPSSFT_ERR_CAPACITY into status.
  * Building block of the unfused, per-iteration host-driven form of the loop.  Returns
  * FPSSFT_ERR_UNSUPPORTED (nothing launched) when one signal's set (k_cap entries and index) does
  * not fit one CTA's shared memory. */
 fpssft_status fpssft_decode(fpssft_plan_t plan, const void* bins, const int32_t* alpha,
                             const int32_t* tau, int32_t* k, void* a, int32_t* count,
-                            int32_t* t0_count, int32_t* status, void* stream);
+                            int32_t* t0_count, int32_t* accepted, int32_t* status, void* stream);
 
 /* Drop entries with |a| <= theta0 and sort each signal's set by linear index (in place).
  * FPSSFT_ERR_UNSUPPORTED as for fpssft_decode. */

@@ -103,7 +103,7 @@ SIGNATURES = {
     "fpssft_recover": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fpssft_recover_host": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fpssft_synth": (_I, [_P, _P, _P, _I, _P, _P, _P, _I, _P, _P]),
-    "fpssft_decode": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fpssft_decode": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fpssft_finalize": (_I, [_P, _P, _P, _P, _P]),
     "fpssft_adjoint": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
     "fpssft_refine_workspace_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),

@@ -22,7 +22,7 @@ class Params:
     theta0: float = 1e-3
     rho: float = 1e-3
     eta: float = 0.05
-    early_stop: bool = True
+    early_stop: int = 1          # 0 none, 1 stop when no line-0 bin passes T0, 2 also when all were decoded
     peel_mode: int = 0
     threads: int = 0
     ctas_per_sm: int = 0
@@ -35,7 +35,7 @@ class Params:
 
     def c(self):
         return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
-                            int(bool(self.early_stop)), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
+                            int(self.early_stop), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
                             int(bool(self.fp64_decisions)), int(self.gather_mode), int(self.fft_path),
                             int(bool(self.amp_average)), int(self.radix_plan), int(self.host_cubes))
 
@@ -236,14 +236,16 @@ class Plan:
                                          int(accumulate), _ptr(bins), _stream(stream)))
         return bins
 
-    def decode(self, bins, alpha, tau, k, a, count, t0_count, status, stream=None):
+    def decode(self, bins, alpha, tau, k, a, count, t0_count, status, accepted=None, stream=None):
         self._sched(alpha, tau, rows=1)
         _need(bins, torch.complex64, "bins")
         self._check_set(k, a, count)
         _need(t0_count, torch.int32, "t0_count")
         _need(status, torch.int32, "status")
+        if accepted is not None:
+            _need(accepted, torch.int32, "accepted")
         _lib.check(self.lib.fpssft_decode(self.handle, _ptr(bins), _ptr(alpha), _ptr(tau), _ptr(k), _ptr(a),
-                                          _ptr(count), _ptr(t0_count), _ptr(status), _stream(stream)))
+                                          _ptr(count), _ptr(t0_count), _ptr(accepted), _ptr(status), _stream(stream)))
 
     def _check_set(self, k, a, count):
         _need(k, torch.int32, "k")

@@ -4,6 +4,10 @@ Noiseless workloads: theta0 = 1e-3 absolute (planted |a| >= 0.5; FP32 residuals 
 ~1e-6), rho = 1e-3, eta = 0.05.  Noisy workloads: a bin of pure noise has standard deviation
 sigma / sqrt(L) (the 1/L DFT of L samples of variance sigma^2), so theta0 = 4 sigma / sqrt(L);
 rho = eta = 0.25.
+
+Stop rule: early_stop = 2, a signal stops after an iteration in which no line-0 bin passes T0 or
+every line-0 bin passing T0 was decoded (the library's default, 1, waits for an iteration that
+finds nothing, one more on noiseless data).
 """
 from __future__ import annotations
 
@@ -41,6 +45,6 @@ def params_for(wl, **over):
     from .api import Params
     th0, rho, eta = threshold_values(wl)
     base = BUDGET.get(wl.name.split("[")[0], dict(T=0, k_cap=1024))
-    kw = dict(T=base["T"], k_cap=base["k_cap"], theta0=th0, rho=rho, eta=eta, early_stop=True)
+    kw = dict(T=base["T"], k_cap=base["k_cap"], theta0=th0, rho=rho, eta=eta, early_stop=2)
     kw.update(over)
     return Params(**kw)

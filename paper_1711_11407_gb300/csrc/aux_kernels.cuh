@@ -131,6 +131,7 @@ struct DecodeArgs {
   float2* a;
   int* count;
   int* t0_count;
+  int* accepted;    // nullable
   int* status;
 };
 
@@ -138,7 +139,7 @@ template <int D>
 __global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
-  __shared__ int s_count, s_t0, s_ovf;
+  __shared__ int s_count, s_t0, s_ovf, s_acc;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
   const int hash_cap = 1 << A.hash_bits;
   SetView set;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
       s_count = 0;
       s_t0 = 0;
       s_ovf = 0;
+      s_acc = 0;
     }
     __syncthreads();
     if (threadIdx.x < D) {
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
     }
     __syncthreads();
     decode_bins<D>(A.bins + (size_t)b * (D + 1) * A.L_max, A.L_max, sh, set, s_ca, s_ct,
-                   A.tab.twiddles + sh.tw_off, A.th, &s_t0, &s_ovf);
+                   A.tab.twiddles + sh.tw_off, A.th, &s_t0, &s_ovf, &s_acc);
     __syncthreads();
     const int cnt = min(s_count, A.k_cap);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs A) {
     if (threadIdx.x == 0) {
       A.count[b] = cnt;
       A.t0_count[b] = s_t0;
+      if (A.accepted) A.accepted[b] = s_acc;
       if (s_ovf) A.status[b] |= kStatusCapacity;
     }
   }

@@ -112,6 +112,7 @@ struct fpssft_plan_s {
   bool tw_smem = true;
   bool prefetch = true;
   bool warp_path = false;   // k_recover_w (register FFT per line) instead of k_recover
+  int warp_mode = 0;        // k_recover_w's request of the next iteration's samples (kWPrefetch, ...)
   bool gm_path = false;     // k_recover with lines and set in global workspace
   bool cluster_path = false;   // k_recover_c (one CTA per line, a cluster of D+1 CTAs per signal)
   bool cluster_gs = false;     // ... with the recovered set in global workspace (GS variant)
@@ -268,7 +269,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
-  if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
+  if (pr.gather_mode < 0 || pr.gather_mode > 4) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 4]");
   if (pr.fft_path < 0 || pr.fft_path > 3) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 3]");
   if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
   if (pr.host_cubes < 0 || pr.host_cubes > 1) return fail(FPSSFT_ERR_INVALID, "host_cubes must be 0 or 1");
@@ -399,6 +400,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       P->smem = wl.total;
       P->tw_smem = true;
       P->prefetch = pr.gather_mode == 3;   // staged in shared memory by cp.async
+      P->warp_mode = pr.gather_mode == 3 ? kWStaged : (pr.gather_mode == 4 ? kWNone : kWPrefetch);
       P->threads = 32 * (D + 1);
     } else if (pr.fft_path == 2) {
       delete P;
@@ -522,7 +524,11 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   fpssft_status st = dispatch_D(D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
     if (P->gm_path) P->threads = std::min(P->threads, 512);
-    const void* kfn = P->warp_path ? (P->prefetch ? (const void*)k_recover_w<DD, true> : (const void*)k_recover_w<DD, false>)
+    auto warp_kfn = [&](int wm) -> const void* {
+      return wm == kWStaged ? (const void*)k_recover_w<DD, kWStaged>
+           : wm == kWNone ? (const void*)k_recover_w<DD, kWNone> : (const void*)k_recover_w<DD, kWPrefetch>;
+    };
+    const void* kfn = P->warp_path ? warp_kfn(P->warp_mode)
                     : P->cluster_path ? (P->cluster_gs ? (P->threads > 512 ? (const void*)k_recover_c<DD, 1024, true> : (const void*)k_recover_c<DD, 512, true>)
                                                         : (P->threads > 512 ? (const void*)k_recover_c<DD, 1024, false> : (const void*)k_recover_c<DD, 512, false>))
                     : P->gm_path ? (const void*)k_recover<DD, 512, true>
@@ -552,6 +558,13 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
     P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
+    // register path, library choice: prefetch the next iteration while one signal per CTA is all
+    // there is (latency); with more signals than resident CTAs, no prefetch (throughput)
+    if (P->warp_path && P->p.gather_mode == 0 && batch > P->grid) {
+      P->warp_mode = kWNone;
+      e2 = ensure_dynamic_smem(warp_kfn(kWNone), P->smem);
+      if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
+    }
     if (P->cluster_path) P->grid = batch * (DD + 1);   // one cluster per signal, not persistent
     if (P->cluster_gs) {   // one slice of global workspace per signal
       const cudaError_t ea = cudaMalloc(&P->d_gm_ws, (size_t)batch * P->gm_stride);
@@ -714,10 +727,12 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
     if (P->warp_path) {
-      if (P->prefetch)
-        k_recover_w<DD, true><<<P->grid, P->threads, P->smem, s>>>(A);
+      if (P->warp_mode == kWStaged)
+        k_recover_w<DD, kWStaged><<<P->grid, P->threads, P->smem, s>>>(A);
+      else if (P->warp_mode == kWNone)
+        k_recover_w<DD, kWNone><<<P->grid, P->threads, P->smem, s>>>(A);
       else
-        k_recover_w<DD, false><<<P->grid, P->threads, P->smem, s>>>(A);
+        k_recover_w<DD, kWPrefetch><<<P->grid, P->threads, P->smem, s>>>(A);
     } else if (P->cluster_path) {
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute attr[1];
@@ -856,8 +871,8 @@ extern "C" fpssft_status fpssft_synth(fpssft_plan_t P, const int32_t* alpha, con
 }
 
 extern "C" fpssft_status fpssft_decode(fpssft_plan_t P, const void* bins, const int32_t* alpha, const int32_t* tau,
-                                       int32_t* k, void* a, int32_t* count, int32_t* t0_count, int32_t* status,
-                                       void* stream) {
+                                       int32_t* k, void* a, int32_t* count, int32_t* t0_count, int32_t* accepted,
+                                       int32_t* status, void* stream) {
   if (!P) return fail(FPSSFT_ERR_INVALID, "null plan");
   if (P->batch == 0) return FPSSFT_OK;
   if (!bins || !alpha || !tau || !k || !a || !count || !t0_count || !status) return fail(FPSSFT_ERR_INVALID, "null device pointer");
@@ -876,6 +891,7 @@ extern "C" fpssft_status fpssft_decode(fpssft_plan_t P, const void* bins, const 
   A.a = static_cast<float2*>(a);
   A.count = count;
   A.t0_count = t0_count;
+  A.accepted = accepted;
   A.status = status;
   return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
@@ -1237,7 +1253,7 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
   if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
-  if (pr.gather_mode < 0 || pr.gather_mode > 3) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 3]");
+  if (pr.gather_mode < 0 || pr.gather_mode > 4) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 4]");
   if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
   if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
 

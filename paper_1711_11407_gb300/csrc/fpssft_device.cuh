@@ -694,14 +694,15 @@ __device__ __noinline__ int classify_fp64(const float2 s0, const float2* sd, con
 }
 
 // Tests T0..T3 on every bin m of the (already peeled) lines; bins of line j at bins[j*line_stride].
-// Adds the number of line-0 bins passing T0 to *t0 and sets *ovf on a capacity overflow.
+// Adds the number of line-0 bins passing T0 to *t0 and of bins decoded (T0..T3 passed) to
+// *accepted, and sets *ovf on a capacity overflow.
 template <int D>
 __device__ __forceinline__ void decode_bins(const float2* bins, int line_stride, const Shape& sh,
                                             const SetView& s, const int* ca, const int* ct,
                                             const float2* __restrict__ tw, const Thresholds& th,
-                                            int* t0, int* ovf) {
+                                            int* t0, int* ovf, int* accepted) {
   const int L = sh.L;
-  int my_t0 = 0;
+  int my_t0 = 0, my_acc = 0;
   bool my_ovf = false;
   for (int m = threadIdx.x; m < L; m += blockDim.x) {
     const float2 s0 = bins[m];
@@ -727,9 +728,11 @@ __device__ __forceinline__ void decode_bins(const float2* bins, int line_stride,
     }
     if (fmod_(msum, sh.fL) != m) continue;                            // T3
     const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tw, th.amp_average != 0);
+    ++my_acc;
     if (!set_insert<D>(s, k, key, a)) my_ovf = true;
   }
   if (my_t0) atomicAdd(t0, my_t0);
+  if (my_acc) atomicAdd(accepted, my_acc);
   if (my_ovf) atomicOr(ovf, 1);
 }
 

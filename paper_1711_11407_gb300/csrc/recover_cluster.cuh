@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
   __shared__ int s_count, s_ovf, s_n;
   __shared__ int s_cnt[kOutBuckets], s_off[kOutBuckets];
   __shared__ int s_t0[2];                     // line-0 bins passing T0, by iteration parity
+  __shared__ int s_acc[2];                    // bins decoded, by iteration parity
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
   __shared__ unsigned char* s_base[kMaxD + 1];  // each rank's dynamic shared memory (generic address)
 
@@ -231,12 +232,15 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     s_ovf = 0;
     s_t0[0] = 0;
     s_t0[1] = 0;
+    s_acc[0] = 0;
+    s_acc[1] = 0;
   }
   cluster.sync();   // every CTA started and initialised before any remote access
 
   int* c_count = GS ? g_count : cluster.map_shared_rank(&s_count, 0);
   int* c_ovf = cluster.map_shared_rank(&s_ovf, 0);
   int* c_t0 = cluster.map_shared_rank(s_t0, 0);
+  int* c_acc = cluster.map_shared_rank(s_acc, 0);
   const float2* x = A.cubes + A.offsets[b];
   int* ok_out = A.out_k + (size_t)b * A.k_cap * D;
   float2* oa_out = A.out_a + (size_t)b * A.k_cap;
@@ -279,7 +283,10 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     const int* ta = sched_t + t * D;
     // slot par was last read after the decode barrier of iteration t-2, before every rank
     // arrived at the peel barrier of t-1, which this rank has passed
-    if (rank == 0 && threadIdx.x == 0) s_t0[par] = 0;
+    if (rank == 0 && threadIdx.x == 0) {
+      s_t0[par] = 0;
+      s_acc[par] = 0;
+    }
     if (threadIdx.x < D) {
       const int d = threadIdx.x;
       s_ca[d] = cmodL(sh, d, al[d]);
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
     FPSSFT_PH(kPhExchange);
 
     const size_t boff = reinterpret_cast<unsigned char*>(bins) - smem;
-    int my_t0 = 0;
+    int my_t0 = 0, my_acc = 0;
     bool my_ovf = false;
     for (int m = m_lo + threadIdx.x; m < m_hi; m += blockDim.x) {
       const float2 s0 = reinterpret_cast<const float2*>(s_base[0] + boff)[m];
@@ -334,18 +341,21 @@ __global__ void __launch_bounds__(MAXT) k_recover_c(RecoverArgs A) {
       }
       if (fmod_(msum, sh.fL) != m) continue;                            // T3
       const float2 a = decoded_amplitude<D>(s0, sd, sh, k, fmod_(psum, sh.fL), tws, A.th.amp_average != 0);
+      ++my_acc;
       const bool ok = GS ? cluster_insert_g<D>(g_la, g_lkey, g_hkey, g_hidx, g_count, A.k_cap, A.hash_bits, key, a)
                          : cluster_insert<D>(s_base, lay, c_count, A.k_cap, A.hash_bits, rank, key, a);
       if (!ok) my_ovf = true;
     }
     if (my_t0) atomicAdd(c_t0 + par, my_t0);
+    if (my_acc) atomicAdd(c_acc + par, my_acc);
     if (my_ovf) atomicOr(c_ovf, 1);
     FPSSFT_PH(kPhDecode);
     cluster.sync();   // every insert landed in every replica
     FPSSFT_PH(kPhExchange);
     n_set = min(GS ? __ldcg(g_count) : *c_count, A.k_cap);
     iters = t + 1;
-    if ((A.early_stop && c_t0[par] == 0) || *c_ovf != 0) break;   // the same verdict on every rank
+    if ((A.early_stop && c_t0[par] == 0) || *c_ovf != 0 || (A.early_stop == 2 && c_acc[par] == c_t0[par]))
+      break;   // the same verdict on every rank
   }
   if (pf) cp_async_wait<0>();
   cluster.sync();   // no rank reads another's shared memory past this point

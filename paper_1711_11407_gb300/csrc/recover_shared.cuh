@@ -15,7 +15,7 @@ template <int D, int MAXT, bool GM = false>
 __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recover(RecoverArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
-  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n;
+  __shared__ int s_sig, s_count, s_t0, s_ovf, s_n, s_acc;
   __shared__ int s_ca[kMaxD], s_ct[kMaxD];
   __shared__ int s_cnt[kOutBuckets], s_off[kOutBuckets];
 
@@ -114,17 +114,20 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
       }
       __syncthreads();
       FPSSFT_PH(kPhGather);
-      if (threadIdx.x == 0) s_t0 = 0;
+      if (threadIdx.x == 0) {
+        s_t0 = 0;
+        s_acc = 0;
+      }
       float2* bins = fft_lines(cur, bufB, D + 1, sh, tw, 1.0f / (float)L, stw);
       FPSSFT_PH(kPhFft);
       peel_set<D>(bins, sh, set, min(s_count, A.k_cap), s_ca, s_ct, tw);
       __syncthreads();
       FPSSFT_PH(kPhPeel);
-      decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf);
+      decode_bins<D>(bins, L, sh, set, s_ca, s_ct, tw, A.th, &s_t0, &s_ovf, &s_acc);
       __syncthreads();
       FPSSFT_PH(kPhDecode);
       iters = t + 1;
-      const bool stop = (A.early_stop && s_t0 == 0) || s_ovf != 0;
+      const bool stop = (A.early_stop && s_t0 == 0) || s_ovf != 0 || (A.early_stop == 2 && s_acc == s_t0);
       if (stop) break;
     }
 

@@ -127,24 +127,31 @@ __device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& s
 // complete and iteration t will find nothing (the early stop): iteration t then does not prefetch
 // t+1.  If the guess is wrong, iteration t+1 gathers its samples synchronously; the results do not
 // depend on the guess.
-template <int D, int R, bool STAGED>
+// WM: how iteration t+1's samples are requested during iteration t.  kWPrefetch: into registers
+// right after the FFT; kWStaged: into shared memory by cp.async; kWNone: not at all (iteration t+1
+// gathers synchronously; with many signals per SM the other CTAs hide that latency, and the
+// registers the prefetch would hold are freed).
+constexpr int kWPrefetch = 0, kWStaged = 1, kWNone = 2;
+
+template <int D, int R, int WM>
 __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
                                          const float2* tws, float2* stg, const float2* __restrict__ x,
                                          const int* sched_a, const int* sched_t, int T, int warp, int lane,
                                          float invL, int* s_ca, int* s_ct, int* s_t0, int* s_ovf, int* s_acc) {
+  constexpr bool STAGED = WM == kWStaged;
   const int L = sh.L;
-  float2 nxt[STAGED ? 1 : R];
+  float2 nxt[WM == kWPrefetch ? R : 1];
   float2* my_stg = stg + warp * L;
   bool have_next = false;      // samples of the current iteration already requested
   bool likely_done = false;    // every T0 bin of the previous iteration was accepted
   FPSSFT_PH(kPhSetup);
-  if (T > 0) {
+  if (T > 0 && WM != kWNone) {   // without prefetch the first iteration gathers like every other
     int alr[D], tar[D];
     sched_row<D>(sh, sched_a, sched_t, alr, tar);
     if (STAGED)
       gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
     else
-      gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
+      gather_line_regs<D, (WM == kWPrefetch ? R : 1)>(nxt, x, sh, alr, tar, warp, lane);
     have_next = true;
   }
   int iters = 0;
@@ -168,19 +175,19 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
       for (int i = 0; i < R; ++i) v[i] = my_stg[lane + 32 * i];
     } else {
 #pragma unroll
-      for (int i = 0; i < R; ++i) v[i] = nxt[STAGED ? 0 : i];
+      for (int i = 0; i < R; ++i) v[i] = nxt[WM == kWPrefetch ? i : 0];
     }
     FPSSFT_PH(kPhGather);
     fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
     FPSSFT_PH(kPhFft);
-    have_next = t + 1 < T && !likely_done;
+    have_next = WM != kWNone && t + 1 < T && !likely_done;
     if (have_next) {
       int alr[D], tar[D];
       sched_row<D>(sh, al + D, ta + D, alr, tar);
       if (STAGED)
         gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
       else
-        gather_line_regs<D, (STAGED ? 1 : R)>(nxt, x, sh, alr, tar, warp, lane);
+        gather_line_regs<D, (WM == kWPrefetch ? R : 1)>(nxt, x, sh, alr, tar, warp, lane);
     }
     __syncthreads();
     FPSSFT_PH(kPhGather);
@@ -195,7 +202,7 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
     __syncthreads();
     FPSSFT_PH(kPhDecode);
     iters = t + 1;
-    const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0;
+    const bool stop = (A.early_stop && *s_t0 == 0) || *s_ovf != 0 || (A.early_stop == 2 && *s_acc == *s_t0);
     if (stop) break;
     likely_done = A.early_stop && *s_acc == *s_t0;
   }
@@ -211,9 +218,10 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
 #define FPSSFT_WS_THREADS_PER_SM 768   // same for the variant that stages the prefetch in shared memory
 #endif
 
-template <int D, bool STAGED>
-__global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_SM : FPSSFT_W_THREADS_PER_SM) / (32 * (D + 1)))
+template <int D, int WM>
+__global__ void __launch_bounds__(32 * (D + 1), (WM == kWStaged ? FPSSFT_WS_THREADS_PER_SM : FPSSFT_W_THREADS_PER_SM) / (32 * (D + 1)))
     k_recover_w(RecoverArgs A) {
+  constexpr bool STAGED = WM == kWStaged;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shape sh;
   __shared__ int s_sig, s_count, s_t0, s_ovf, s_n, s_acc;
@@ -278,10 +286,10 @@ __global__ void __launch_bounds__(32 * (D + 1), (STAGED ? FPSSFT_WS_THREADS_PER_
     const int* sched_t = A.tau + (size_t)b * A.sched_stride;
     int iters = 0;
     switch (R) {
-      case 1: iters = iterate_w<D, 1, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-      case 2: iters = iterate_w<D, 2, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-      case 4: iters = iterate_w<D, 4, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
-      default: iters = iterate_w<D, 8, STAGED>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 1: iters = iterate_w<D, 1, WM>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 2: iters = iterate_w<D, 2, WM>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      case 4: iters = iterate_w<D, 4, WM>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
+      default: iters = iterate_w<D, 8, WM>(A, sh, set, bins, tws, stg, x, sched_a, sched_t, T, warp, lane, invL, s_ca, s_ct, &s_t0, &s_ovf, &s_acc); break;
     }
     FPSSFT_PH_ITERS(iters);
 

@@ -38,6 +38,7 @@ class PlainRecoverer:
         a = torch.zeros((1, plan.k_cap), dtype=torch.complex64, device=dev)
         count = torch.zeros(1, dtype=torch.int32, device=dev)
         t0 = torch.zeros(1, dtype=torch.int32, device=dev)
+        acc = torch.zeros(1, dtype=torch.int32, device=dev)
         status = torch.zeros(1, dtype=torch.int32, device=dev)
         off = torch.zeros(1, dtype=torch.int64, device=dev)
         iters = 0
@@ -52,9 +53,11 @@ class PlainRecoverer:
             with nvtx.range("peel"):
                 plan.synth(al, ta, k, a, count, accumulate=-1, bins=bins)
             with nvtx.range("decode_merge"):
-                plan.decode(bins, al, ta, k, a, count, t0, status)
+                plan.decode(bins, al, ta, k, a, count, t0, status, accepted=acc)
             iters = t + 1
-            if (self.params.early_stop and int(t0.item()) == 0) or int(status.item()) != 0:
+            n_t0 = int(t0.item())
+            if (self.params.early_stop and n_t0 == 0) or int(status.item()) != 0 or \
+                    (self.params.early_stop == 2 and int(acc.item()) == n_t0):
                 break
         plan.finalize(k, a, count)
         n = int(count.item())

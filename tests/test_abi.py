@@ -52,7 +52,7 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"threads": 48}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"threads": 2048}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
-    (2, 1, [8, 8], {"gather_mode": 4}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"gather_mode": 5}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"fft_path": 4}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"radix_plan": -1}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"radix_plan": 4}, _lib.ERR_INVALID),
@@ -94,11 +94,13 @@ def test_every_call_rejects_a_null_plan_or_pointer_on_the_host():
         "fpssft_recover": (Z,) * 12,
         "fpssft_recover_host": (Z,) * 12,
         "fpssft_synth": (Z, Z, Z, 1, Z, Z, Z, 0, Z, Z),
-        "fpssft_decode": (Z,) * 10,
+        "fpssft_decode": (Z,) * 11,
         "fpssft_finalize": (Z,) * 5,
         "fpssft_adjoint": (Z, 0, Z, Z, Z, Z, 1, Z, Z, Z, Z),
         "fpssft_probe_gather": (Z, 1024, 1, 256, 0, 0, Z, Z),
         "fpssft_recover_noalloc": (2, 1, Z, Z) + (Z,) * 11,
+        "fpssft_refine": (Z, Z, Z, Z, 1, Z, Z, Z, 1, 1e-7, Z, 0, Z, Z),
+        "fpssft_refine_workspace_size": (Z, Z),
     }
     for name, args in cases.items():
         assert getattr(lib, name)(*args) == _lib.ERR_INVALID, name

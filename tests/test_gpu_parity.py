@@ -121,6 +121,27 @@ def test_recover_matches_oracle(case):
         assert int(out.status[b]) == ref.status
 
 
+@pytest.mark.parametrize("fft_path,gather_mode", [(1, 0), (2, 1), (2, 3), (2, 4), (3, 0)])
+def test_decoded_stop_matches_the_oracle_on_every_kernel_path(fft_path, gather_mode):
+    """early_stop = 2 (stop after an iteration whose line-0 T0 bins were all decoded): same sets,
+    iteration counts and status as the oracle under the same reading, on every kernel path, one
+    iteration earlier than the first reading on noiseless signals."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=24)
+    for es in (1, 2):
+        p = configs.params_for(wl, early_stop=es, fft_path=fft_path, gather_mode=gather_mode)
+        plan = Plan(wl.dims, p)
+        out = plan.recover(*to_dev(wl))
+        torch.cuda.synchronize()
+        for b in range(wl.batch):
+            T = int(plan.T[b])
+            ref = O.recover(wl.cube(b), wl.alpha[b, :T], wl.tau[b, :T], oracle_params(p, T))
+            k, a = out.signal(b)
+            assert_same_set(k, a, ref, f"early_stop {es} path {fft_path} signal {b}")
+            assert int(out.iters[b]) == ref.iters and int(out.status[b]) == ref.status
+        plan.close()
+
+
 def test_recover_full_uneven_batch_sampled_against_oracle():
     """4096 uneven 2-D signals in the launch configuration the benchmark times; 40 sampled signals
     against the oracle, every signal against its planted spectrum."""
@@ -662,8 +683,8 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
     wl = small_batch([dims], 3, K=lambda N: K, T=T, seed=2000 + seed)
     refs = {}
     # the last entry forces the cluster path's set into global workspace (k_cap beyond shared memory)
-    for path, gm, kcap in ((1, 1, 2 * K + 8), (1, 3, 2 * K + 8), (2, 1, 2 * K + 8), (3, 1, 2 * K + 8),
-                           (3, 3, 2 * K + 8), (3, 1, 16000)):
+    for path, gm, kcap in ((1, 1, 2 * K + 8), (1, 3, 2 * K + 8), (2, 1, 2 * K + 8), (2, 4, 2 * K + 8),
+                           (3, 1, 2 * K + 8), (3, 3, 2 * K + 8), (3, 1, 16000)):
         p = configs.params_for(wl, T=T, k_cap=kcap, fft_path=path, gather_mode=gm)
         try:
             plan = Plan(wl.dims, p)
@@ -690,7 +711,8 @@ def test_redecoded_frequencies_accumulate_their_residual_like_the_oracle(fft_pat
     spectrum; keeping or replacing the old amplitude would leave delta or -delta."""
     from paper_1711_11407_gb300.api import Plan
     wl = small_batch([(32, 64)], 3, K=lambda N: 12, T=8, seed=11)    # L = 64: every path applies
-    p = configs.params_for(wl, T=8, k_cap=k_cap, fft_path=fft_path)
+    # the first stop reading, so that the iteration after the residuals' decode is run and compared too
+    p = configs.params_for(wl, T=8, k_cap=k_cap, fft_path=fft_path, early_stop=1)
     plan = Plan(wl.dims, p)
     assert plan.info["fft_path"] == fft_path
     cubes, offs, al, ta = to_dev(wl)
