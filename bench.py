@@ -362,6 +362,46 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def other_stop_rule(wl, p, cubes, offs, alpha, tau, stream, flush, world, dev, steps=200):
+    """The same launch timed with the other early-stop reading (1 <-> 2), for comparison: 1 stops
+    after an iteration in which no line-0 bin passes T0, 2 already after an iteration whose line-0
+    bins passing T0 were all decoded."""
+    import torch
+    from dataclasses import replace
+
+    from oracle import fpssft_oracle as O
+    from paper_1711_11407_gb300.api import Plan
+    rule = 1 if p.early_stop == 2 else 2
+    plan = Plan(wl.dims, replace(p, early_stop=rule))
+    out = plan.alloc_output(dev)
+    with torch.cuda.stream(stream):
+        plan.recover(cubes, offs, alpha, tau, out=out)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            plan.recover(cubes, offs, alpha, tau, out=out)
+        for _ in range(3):
+            g.replay()
+        stream.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    step = max_over_ranks(sum(ms), world, dev) / steps
+    ks, cnt, iters = out.k.cpu().numpy(), out.count.cpu().numpy(), out.iters.cpu().numpy()
+    ok = sum(int(np.array_equal(O.linear_index(ks[b, :cnt[b]].astype(np.int64), tuple(int(v) for v in wl.dims[b])),
+                                np.sort(O.linear_index(wl.k_true[b], tuple(int(v) for v in wl.dims[b])))))
+             for b in range(wl.batch))
+    plan.close()
+    return {"early_stop": rule, "ms_per_step": step, "value": job_rate(wl.batch, world, step), "steps": steps,
+            "mean_iterations": float(np.mean(iters)), "exact_support_success": ok / wl.batch}
+
+
 def refine_leg(args, wl, plan, cubes, offs, alpha, tau, out, stream):
     """Least-squares amplitude refinement (fpssft_refine) after the recovery, over the first R
     schedule rows: timed on the device (projection of the rows plus the CG loop, per batch), and
@@ -589,6 +629,8 @@ def main():
                         "per second the probe moves for the same mix of single and pair accesses"}
 
     refine_rec = refine_leg(args, wl, plan, cubes, offs, alpha, tau, out, stream) if args.refine_rows > 0 else None
+    other_stop = other_stop_rule(wl, p, cubes, offs, alpha, tau, stream, flush, world, dev) \
+        if p.early_stop in (1, 2) and not args.quick else None
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -608,6 +650,9 @@ def main():
             "clocks": clk.summary()}
     if refine_rec is not None:
         line["refine"] = refine_rec
+    line["config"]["early_stop"] = int(p.early_stop)
+    if other_stop is not None:
+        line["other_stop_rule"] = other_stop
 
     if not args.quick:
         # ---- end to end through the host-buffer call ------------------------------------------
