@@ -92,7 +92,10 @@ typedef struct {
                         computes.  On the register-FFT path modes 1 and 2 prefetch the next
                         iteration into registers instead; 4 = synchronous through L1 with no
                         prefetch (on the register-FFT path the library's choice when the batch has
-                        more signals than resident CTAs; elsewhere the same as 1) */
+                        more signals than resident CTAs; elsewhere the same as 1); 5 = as 4, with the
+                        next iteration's samples hinted into L2 (prefetch.global.L2) right after the
+                        FFT (register-FFT path: the library's choice for batches that fit the
+                        resident CTAs; elsewhere the same as 1) */
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
                         FFT (every L of the batch in {32, 64, 128, 256}), 3 = one CTA per line, the

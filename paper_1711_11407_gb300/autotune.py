@@ -6,7 +6,8 @@ Candidates are the valid combinations of
                line, a cluster of D+1 CTAs per signal; only for lines of 512 points or more),
   gather_mode  1 (synchronous through L1), 2 (L2 only), 3 (asynchronous prefetch: cp.async into
                shared memory; on path 2 it replaces the register prefetch) or, on path 2, 4 (no
-               prefetch of the next iteration: throughput over latency),
+               prefetch of the next iteration: throughput over latency) or 5 (4 with the next
+               iteration's samples hinted into L2),
   threads      CTA size for paths 1 and 3 (path 2 is fixed at 32 (D+1)),
   radix_plan   the order of the shared-memory FFT's mixed-radix stages (paths 1 and 3): tried for
                the fastest of the candidates above, each plan whose stage sequence differs from
@@ -47,7 +48,7 @@ def candidates(dims, params: Params):
     L_max = max(Ls) if Ls else 1
     out = []
     if warp_ok:
-        for gm in (1, 3, 4):
+        for gm in (1, 3, 4, 5):
             out.append(replace(params, fft_path=2, gather_mode=gm, threads=0))
     for th in (128, 256, 512, 1024):
         if th > 4 * max(32, L_max) or (th == 1024 and L_max < 512):

@@ -269,7 +269,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
-  if (pr.gather_mode < 0 || pr.gather_mode > 4) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 4]");
+  if (pr.gather_mode < 0 || pr.gather_mode > 5) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 5]");
   if (pr.fft_path < 0 || pr.fft_path > 3) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 3]");
   if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
   if (pr.host_cubes < 0 || pr.host_cubes > 1) return fail(FPSSFT_ERR_INVALID, "host_cubes must be 0 or 1");
@@ -400,7 +400,8 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
       P->smem = wl.total;
       P->tw_smem = true;
       P->prefetch = pr.gather_mode == 3;   // staged in shared memory by cp.async
-      P->warp_mode = pr.gather_mode == 3 ? kWStaged : (pr.gather_mode == 4 ? kWNone : kWPrefetch);
+      P->warp_mode = pr.gather_mode == 3 ? kWStaged : pr.gather_mode == 4 ? kWNone
+                   : pr.gather_mode == 5 ? kWL2Hint : kWPrefetch;
       P->threads = 32 * (D + 1);
     } else if (pr.fft_path == 2) {
       delete P;
@@ -526,7 +527,8 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (P->gm_path) P->threads = std::min(P->threads, 512);
     auto warp_kfn = [&](int wm) -> const void* {
       return wm == kWStaged ? (const void*)k_recover_w<DD, kWStaged>
-           : wm == kWNone ? (const void*)k_recover_w<DD, kWNone> : (const void*)k_recover_w<DD, kWPrefetch>;
+           : wm == kWNone ? (const void*)k_recover_w<DD, kWNone>
+           : wm == kWL2Hint ? (const void*)k_recover_w<DD, kWL2Hint> : (const void*)k_recover_w<DD, kWPrefetch>;
     };
     const void* kfn = P->warp_path ? warp_kfn(P->warp_mode)
                     : P->cluster_path ? (P->cluster_gs ? (P->threads > 512 ? (const void*)k_recover_c<DD, 1024, true> : (const void*)k_recover_c<DD, 512, true>)
@@ -558,11 +560,11 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
     P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
-    // register path, library choice: prefetch the next iteration while one signal per CTA is all
-    // there is (latency); with more signals than resident CTAs, no prefetch (throughput)
-    if (P->warp_path && P->p.gather_mode == 0 && batch > P->grid) {
-      P->warp_mode = kWNone;
-      e2 = ensure_dynamic_smem(warp_kfn(kWNone), P->smem);
+    // register path, library choice: with more signals than resident CTAs no prefetch (the other
+    // CTAs hide the gather's latency; throughput), else the next iteration hinted into L2 (latency)
+    if (P->warp_path && P->p.gather_mode == 0) {
+      P->warp_mode = batch > P->grid ? kWNone : kWL2Hint;
+      e2 = ensure_dynamic_smem(warp_kfn(P->warp_mode), P->smem);
       if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
     }
     if (P->cluster_path) P->grid = batch * (DD + 1);   // one cluster per signal, not persistent
@@ -731,6 +733,8 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
         k_recover_w<DD, kWStaged><<<P->grid, P->threads, P->smem, s>>>(A);
       else if (P->warp_mode == kWNone)
         k_recover_w<DD, kWNone><<<P->grid, P->threads, P->smem, s>>>(A);
+      else if (P->warp_mode == kWL2Hint)
+        k_recover_w<DD, kWL2Hint><<<P->grid, P->threads, P->smem, s>>>(A);
       else
         k_recover_w<DD, kWPrefetch><<<P->grid, P->threads, P->smem, s>>>(A);
     } else if (P->cluster_path) {
@@ -1253,7 +1257,7 @@ extern "C" fpssft_status fpssft_recover_noalloc(int D, int batch, const int64_t*
   if (pr.T < 0) return fail(FPSSFT_ERR_INVALID, "T must be >= 0");
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
-  if (pr.gather_mode < 0 || pr.gather_mode > 4) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 4]");
+  if (pr.gather_mode < 0 || pr.gather_mode > 5) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 5]");
   if (pr.threads < 0 || pr.threads > 512 || (pr.threads % 32) != 0) return fail(FPSSFT_ERR_INVALID, "threads must be a multiple of 32 in [0, 512]");
   if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
 

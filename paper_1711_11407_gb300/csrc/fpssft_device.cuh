@@ -306,33 +306,33 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ in, float2*
 }
 
 // Any radix (used for prime factors other than 2, 3, 5): O(R^2) per butterfly, inputs re-read
-// from shared memory.
+// from shared memory.  One work item per output (line, butterfly j, output q), so that a stage
+// with few butterflies -- a large prime R, or R = L for a prime line length -- still spreads its
+// L R multiply-adds over every thread of the CTA.
 __device__ __forceinline__ void fft_stage_generic(const float2* __restrict__ in, float2* __restrict__ out,
                                                   int L, int nlines, int Ns, int R, int tstep, const FastDiv& fnb,
                                                   const FastDiv& fns, const float2* __restrict__ tw,
                                                   const float2* __restrict__ stw, float sc) {
   const int nb = fnb.d;
   const int rstep = nb;              // exp(-j 2 pi x / R) = tw[(x mod R) * L / R]
-  const int total = nlines * nb;
+  const int total = nlines * L;      // nlines * nb * R outputs
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int line = fdiv(w, fnb);
-    const int j = w - line * nb;
+    const int line = w / L;
+    const int r = w - line * L;      // r = q nb + j
+    const int q = fdiv(r, fnb);
+    const int j = r - q * nb;
     const float2* src = in + line * L;
-    float2* dst = out + line * L;
     const int k = fmod_(j, fns);
-    const int base = (j - k) * R + k;
-    for (int q = 0; q < R; ++q) {
-      float2 acc = make_float2(0.f, 0.f);
-      int x = 0;                     // (i q) mod R, advanced incrementally
-      for (int i = 0; i < R; ++i) {
-        float2 v = src[j + i * nb];
-        if (k != 0 && i != 0) v = cmul(v, stw ? stw[i * Ns + k - 1] : tw[i * k * tstep]);
-        acc = cadd(acc, cmul(v, tw[x * rstep]));
-        x += q;
-        if (x >= R) x -= R;
-      }
-      dst[base + q * Ns] = cscale(acc, sc);
+    float2 acc = make_float2(0.f, 0.f);
+    int x = 0;                       // (i q) mod R, advanced incrementally
+    for (int i = 0; i < R; ++i) {
+      float2 v = src[j + i * nb];
+      if (k != 0 && i != 0) v = cmul(v, stw ? stw[i * Ns + k - 1] : tw[i * k * tstep]);
+      acc = cadd(acc, cmul(v, tw[x * rstep]));
+      x += q;
+      if (x >= R) x -= R;
     }
+    out[line * L + (j - k) * R + k + q * Ns] = cscale(acc, sc);
   }
 }
 
@@ -415,23 +415,22 @@ __device__ __forceinline__ void fft_stage_line_generic(const float2* __restrict_
                                                        int Ns, int R, const FastDiv& fns, const float2* __restrict__ tw,
                                                        const float2* __restrict__ stw, bool pin, bool pout, float sc) {
   const int nb = L / R;
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+  for (int r = threadIdx.x; r < L; r += blockDim.x) {   // one output (butterfly j, output q) per item
+    const int q = r / nb;
+    const int j = r - q * nb;
     const int k = fmod_(j, fns);
-    const int base = (j - k) * R + k;
-    for (int q = 0; q < R; ++q) {
-      float2 acc = make_float2(0.f, 0.f);
-      int x = 0;                     // (i q) mod R
-      for (int i = 0; i < R; ++i) {
-        const int qi = j + i * nb;
-        float2 v = in[pin ? padq(qi) : qi];
-        if (k != 0 && i != 0) v = cmul(v, stw[i * Ns + k - 1]);
-        acc = cadd(acc, cmul(v, tw[x * nb]));   // exp(-j 2 pi x / R) = tw[x L / R]
-        x += q;
-        if (x >= R) x -= R;
-      }
-      const int qo = base + q * Ns;
-      out[pout ? padq(qo) : qo] = cscale(acc, sc);
+    float2 acc = make_float2(0.f, 0.f);
+    int x = 0;                       // (i q) mod R
+    for (int i = 0; i < R; ++i) {
+      const int qi = j + i * nb;
+      float2 v = in[pin ? padq(qi) : qi];
+      if (k != 0 && i != 0) v = cmul(v, stw[i * Ns + k - 1]);
+      acc = cadd(acc, cmul(v, tw[x * nb]));   // exp(-j 2 pi x / R) = tw[x L / R]
+      x += q;
+      if (x >= R) x -= R;
     }
+    const int qo = (j - k) * R + k + q * Ns;
+    out[pout ? padq(qo) : qo] = cscale(acc, sc);
   }
 }
 
@@ -1070,6 +1069,32 @@ __device__ __forceinline__ void gather_line_regs(float2 (&v)[R], const float2* _
 #pragma unroll
     for (int d = 0; d < D; ++d) base += n[d] * sh.strides[d];
     v[i] = __ldg(x + base);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      n[d] += stepn[d];
+      if (n[d] >= sh.dims[d]) n[d] -= sh.dims[d];
+    }
+  }
+}
+
+// Request line j's samples into L2 without waiting for them (prefetch.global.L2).  No register
+// receives them, so the CTA barriers that follow do not wait for them as they wait for
+// outstanding loads; the next iteration's synchronous gather then finds them in L2.
+template <int D, int R>
+__device__ __forceinline__ void prefetch_line_l2(const float2* __restrict__ x, const Shape& sh, const int* al,
+                                                 const int* ta, int j, int lane) {
+  int n[D], stepn[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    n[d] = fmod_(al[d] * lane + ta[d] + (j == d + 1 ? 1 : 0), sh.fdims[d]);
+    stepn[d] = fmod_(al[d] * 32, sh.fdims[d]);
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int base = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) base += n[d] * sh.strides[d];
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(x + base));
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       n[d] += stepn[d];

@@ -52,6 +52,27 @@ __device__ __forceinline__ void sched_row(const Shape& sh, const int* al, const 
   }
 }
 
+// A schedule row as read from memory, loaded an iteration before its gather so that the sample
+// addresses do not wait for the row (the L2-hint mode's pipeline).
+template <int D>
+struct RawRow {
+  int a[D], t[D];
+  __device__ __forceinline__ void load(const int* al, const int* ta) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      a[d] = __ldg(al + d);
+      t[d] = __ldg(ta + d);
+    }
+  }
+  __device__ __forceinline__ void sanitize(const Shape& sh, int* alr, int* tar) const {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      alr[d] = fmod_(a[d] & 0x3fffffff, sh.fdims[d]);
+      tar[d] = fmod_(t[d] & 0x3fffffff, sh.fdims[d]);
+    }
+  }
+};
+
 template <int D>
 __device__ __forceinline__ void peel_set_w(float2* bins, const Shape& sh, const BucketSet& s, int count, const int* ca,
                                            const int* ct, const float2* __restrict__ tw) {
@@ -130,8 +151,11 @@ __device__ __forceinline__ void decode_bins_w(const float2* bins, const Shape& s
 // WM: how iteration t+1's samples are requested during iteration t.  kWPrefetch: into registers
 // right after the FFT; kWStaged: into shared memory by cp.async; kWNone: not at all (iteration t+1
 // gathers synchronously; with many signals per SM the other CTAs hide that latency, and the
-// registers the prefetch would hold are freed).
-constexpr int kWPrefetch = 0, kWStaged = 1, kWNone = 2;
+// registers the prefetch would hold are freed); kWL2Hint: as kWNone, but the samples are hinted
+// into L2 right after the FFT and the schedule rows are read an iteration ahead (few signals per
+// SM: the synchronous gather then waits for L2, not DRAM).  A CTA barrier waits for the loads its
+// threads have outstanding, so register prefetches only overlap the work before the next barrier.
+constexpr int kWPrefetch = 0, kWStaged = 1, kWNone = 2, kWL2Hint = 3;
 
 template <int D, int R, int WM>
 __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, const BucketSet& set, float2* bins,
@@ -144,8 +168,15 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
   float2* my_stg = stg + warp * L;
   bool have_next = false;      // samples of the current iteration already requested
   bool likely_done = false;    // every T0 bin of the previous iteration was accepted
+  constexpr bool HINT = WM == kWL2Hint;
+  constexpr bool SYNC = WM == kWNone || WM == kWL2Hint;   // every iteration gathers at its start
   FPSSFT_PH(kPhSetup);
-  if (T > 0 && WM != kWNone) {   // without prefetch the first iteration gathers like every other
+  RawRow<D> cur, nx;   // kWL2Hint: schedule rows t and t+1
+  if (HINT) {
+    if (T > 0) cur.load(sched_a, sched_t);
+    if (T > 1) nx.load(sched_a + D, sched_t + D);
+  }
+  if (T > 0 && !SYNC) {   // without prefetch the first iteration gathers like every other
     int alr[D], tar[D];
     sched_row<D>(sh, sched_a, sched_t, alr, tar);
     if (STAGED)
@@ -160,14 +191,17 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
     const int* ta = sched_t + t * D;
     if (threadIdx.x < D) {
       const int d = threadIdx.x;
-      s_ca[d] = cmodL(sh, d, al[d]);
-      s_ct[d] = cmodL(sh, d, ta[d]);
+      s_ca[d] = cmodL(sh, d, HINT ? cur.a[d] : al[d]);
+      s_ct[d] = cmodL(sh, d, HINT ? cur.t[d] : ta[d]);
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) set.head[m] = -1;
     float2 v[R];
     if (!have_next) {
       int alr[D], tar[D];
-      sched_row<D>(sh, al, ta, alr, tar);
+      if (HINT)
+        cur.sanitize(sh, alr, tar);
+      else
+        sched_row<D>(sh, al, ta, alr, tar);
       gather_line_regs<D, R>(v, x, sh, alr, tar, warp, lane);
     } else if (STAGED) {
       cp_async_wait<0>();
@@ -180,7 +214,7 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
     FPSSFT_PH(kPhGather);
     fft_store_w<D, R>(v, bins, sh, tws, warp, lane, invL);    // consumes v: the reads above are done
     FPSSFT_PH(kPhFft);
-    have_next = WM != kWNone && t + 1 < T && !likely_done;
+    have_next = !SYNC && t + 1 < T && !likely_done;
     if (have_next) {
       int alr[D], tar[D];
       sched_row<D>(sh, al + D, ta + D, alr, tar);
@@ -188,6 +222,15 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
         gather_line_async<D, R>(my_stg, x, sh, alr, tar, warp, lane);
       else
         gather_line_regs<D, (WM == kWPrefetch ? R : 1)>(nxt, x, sh, alr, tar, warp, lane);
+    }
+    if (HINT) {
+      if (t + 1 < T) {
+        int alr[D], tar[D];
+        nx.sanitize(sh, alr, tar);
+        prefetch_line_l2<D, R>(x, sh, alr, tar, warp, lane);
+      }
+      cur = nx;                                                // row t is no longer needed
+      if (t + 2 < T) nx.load(sched_a + (t + 2) * D, sched_t + (t + 2) * D);
     }
     __syncthreads();
     FPSSFT_PH(kPhGather);

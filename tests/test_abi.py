@@ -52,7 +52,7 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"threads": 48}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"threads": 2048}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"peel_mode": 1}, _lib.ERR_UNSUPPORTED),
-    (2, 1, [8, 8], {"gather_mode": 5}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"gather_mode": 6}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"fft_path": 4}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"radix_plan": -1}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"radix_plan": 4}, _lib.ERR_INVALID),

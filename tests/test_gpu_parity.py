@@ -121,7 +121,7 @@ def test_recover_matches_oracle(case):
         assert int(out.status[b]) == ref.status
 
 
-@pytest.mark.parametrize("fft_path,gather_mode", [(1, 0), (2, 1), (2, 3), (2, 4), (3, 0)])
+@pytest.mark.parametrize("fft_path,gather_mode", [(1, 0), (2, 1), (2, 3), (2, 4), (2, 5), (3, 0)])
 def test_decoded_stop_matches_the_oracle_on_every_kernel_path(fft_path, gather_mode):
     """early_stop = 2 (stop after an iteration whose line-0 T0 bins were all decoded): same sets,
     iteration counts and status as the oracle under the same reading, on every kernel path, one
@@ -455,6 +455,39 @@ def test_autotuned_launch_computes_the_same_sets(name, batch):
         assert torch.allclose(ref.a[b, :n], got.a[b, :n], rtol=AMP_TOL, atol=0)
 
 
+@pytest.mark.parametrize("fft_path", [1, 3])
+def test_prime_line_lengths_match_the_oracle(fft_path):
+    """A line length that is a large prime (1009) or has one (2 x 509, 97 x 101 = 9797): the generic
+    radix stage, one work item per output, gives the oracle's line DFTs and sets."""
+    from paper_1711_11407_gb300 import _lib
+    from paper_1711_11407_gb300.api import Plan
+    for shapes in ([(1009, 1009)], [(509, 2, 2)], [(97, 101)]):
+        wl = small_batch(shapes, 2, K=lambda N: 20, T=6, seed=23)
+        p = configs.params_for(wl, T=6, k_cap=64, fft_path=fft_path)
+        try:
+            plan = Plan(wl.dims, p)
+        except _lib.FpssftError as e:                    # 9797-point lines exceed one CTA (path 3)
+            assert fft_path == 3 and e.status == _lib.ERR_UNSUPPORTED
+            continue
+        t = to_dev(wl)
+        out = plan.recover(*t)
+        bins = plan.project(t[0], t[1], t[2][:, :1].contiguous(), t[3][:, :1].contiguous()).cpu().numpy() \
+            if plan.info["global_workspace"] == 0 or fft_path == 1 else None
+        torch.cuda.synchronize()
+        for b in range(wl.batch):
+            L = int(plan.L[b])
+            if bins is not None:
+                ref = O.project(wl.cube(b), wl.alpha[b, 0], wl.tau[b, 0])
+                for j in range(wl.D + 1):
+                    e = np.linalg.norm(bins[b, 0, j, :L] - ref[j]) / np.linalg.norm(ref[j])
+                    assert e <= BIN_TOL, f"L = {L}: line bins rel L2 {e:.2e}"
+            ref = O.recover(wl.cube(b), wl.alpha[b], wl.tau[b], oracle_params(p, 6))
+            k, a = out.signal(b)
+            assert_same_set(k, a, ref, f"L = {L} path {fft_path} signal {b}")
+            assert int(out.iters[b]) == ref.iters
+        plan.close()
+
+
 @pytest.mark.parametrize("radix_plan", [1, 2, 3])
 @pytest.mark.parametrize("fft_path", [1, 3])
 def test_every_radix_plan_matches_the_oracle(radix_plan, fft_path):
@@ -683,7 +716,7 @@ def test_random_shapes_match_oracle_on_every_kernel_path(seed):
     wl = small_batch([dims], 3, K=lambda N: K, T=T, seed=2000 + seed)
     refs = {}
     # the last entry forces the cluster path's set into global workspace (k_cap beyond shared memory)
-    for path, gm, kcap in ((1, 1, 2 * K + 8), (1, 3, 2 * K + 8), (2, 1, 2 * K + 8), (2, 4, 2 * K + 8),
+    for path, gm, kcap in ((1, 1, 2 * K + 8), (1, 3, 2 * K + 8), (2, 1, 2 * K + 8), (2, 4, 2 * K + 8), (2, 5, 2 * K + 8),
                            (3, 1, 2 * K + 8), (3, 3, 2 * K + 8), (3, 1, 16000)):
         p = configs.params_for(wl, T=T, k_cap=kcap, fft_path=path, gather_mode=gm)
         try:
