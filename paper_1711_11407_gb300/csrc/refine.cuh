@@ -114,10 +114,12 @@ __global__ void __launch_bounds__(256) k_refine_normal(RefineNormalArgs A) {
         if (on_grid<D>(sh, k)) project_entry<D>(bins, L, sh, k, vb[i], s_ca, s_ct, tw, sign);
       }
       __syncthreads();
+      float sqr = 0.f;   // this thread's few bins of the row in FP32, the sums over rows and threads in FP64
       for (int i = threadIdx.x; i < (D + 1) * L; i += blockDim.x) {
         const float2 q = bins[i];
-        sq += (double)q.x * q.x + (double)q.y * q.y;
+        sqr = fmaf(q.x, q.x, fmaf(q.y, q.y, sqr));
       }
+      sq += (double)sqr;
       if (A.want_g) {
         // g_i += sum_j conj(W^(p + [j > 0] c_{j-1} k_{j-1})) bins_j(m(k_i)); conj(W^q) = tw[q]
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
