@@ -30,7 +30,10 @@ Readings of points the paper leaves open (each one is stated where it is used):
 
 Every function here is pinned by tests/pins.py against the paper's closed forms, brute force or
 printed values.  Parity unpinned: the outcome on noisy inputs, which the paper does not model; on
-those the CUDA path is compared with this oracle one iteration at a time from the same set.
+those the CUDA path is compared with this oracle one iteration at a time from the same set, and
+over whole runs signal by signal.  Beyond the loop: FP64 least-squares amplitudes over many lines
+(`refine_lstsq`, the counterpart of the library's refinement) and several offset sets per slope
+(`recover_offset_sets`), both pinned the same way.
 """
 from __future__ import annotations
 
