@@ -14,8 +14,8 @@ Candidates are the valid combinations of
                the default for some line length of the batch (fpssft_fft_stages).
 Each candidate is timed on the caller's own inputs with CUDA events (warm-up first, a buffer larger
 than L2 written between timed launches); the fastest wins.  Results are cached in a JSON file keyed
-by GPU name, D, the sorted set of shapes, k_cap and T, so a batch with the same layout is not
-re-tuned.  Tuning never changes what is computed, only how it is launched.
+by GPU name, D, the sorted set of shapes, k_cap, T and the stop rule, so a batch with the same
+layout is not re-tuned.  Tuning never changes what is computed, only how it is launched.
 """
 from __future__ import annotations
 
@@ -37,7 +37,7 @@ def cache_key(dims, params: Params, gpu_name: str):
     dims = np.asarray(dims, np.int64)
     shapes = sorted({tuple(int(v) for v in d) for d in dims})
     return json.dumps({"gpu": gpu_name, "D": int(dims.shape[1]), "shapes": shapes, "k_cap": int(params.k_cap),
-                       "T": int(params.T)}, sort_keys=True)
+                       "T": int(params.T), "early_stop": int(params.early_stop)}, sort_keys=True)
 
 
 def candidates(dims, params: Params):

@@ -26,6 +26,8 @@ def test_cache_key_ignores_batch_order_and_size():
     assert a == b
     assert a != autotune.cache_key(np.array([[64, 64]]), p, "GB300")
     assert a != autotune.cache_key(np.array([[64, 64], [128, 128]]), Params(T=0, k_cap=256), "GB300")
+    # the stop rule changes how many iterations a signal runs, and with it the best launch
+    assert a != autotune.cache_key(np.array([[64, 64], [128, 128]]), Params(T=0, k_cap=512, early_stop=2), "GB300")
 
 
 def test_cache_hit_returns_the_stored_choice_without_timing(tmp_path, monkeypatch):
