@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--gather-mode", type=int, default=0)
     ap.add_argument("--fft-path", type=int, default=0)
+    ap.add_argument("--cluster-set", type=int, default=0, help="path 3: 1 set in shared memory, 2 in global workspace")
     ap.add_argument("--early-stop", type=int, default=None,
                     help="stop rule (0 none, 1 after an iteration with no line-0 bin passing T0, 2 also after "
                          "an iteration whose line-0 bins passing T0 were all decoded); default: the workload's")
@@ -515,7 +516,7 @@ def main():
     wl = synth.make_workload(args.workload, seed=seed, batch=args.batch)
     over = {} if args.early_stop is None else {"early_stop": args.early_stop}
     p = configs.params_for(wl, **over, threads=args.threads, ctas_per_sm=args.ctas_per_sm, gather_mode=args.gather_mode,
-                           fft_path=args.fft_path)
+                           fft_path=args.fft_path, cluster_set=args.cluster_set)
     from paper_1711_11407_gb300.api import l2_fetch_granularity
     l2_prev = l2_fetch_granularity(args.l2_fetch)
     cubes = torch.from_numpy(wl.cubes).to(dev)
@@ -523,7 +524,8 @@ def main():
     alpha = torch.from_numpy(wl.alpha).to(dev)
     tau = torch.from_numpy(wl.tau).to(dev)
     tuning = None
-    if not args.no_autotune and args.threads == 0 and args.fft_path == 0 and args.gather_mode == 0:
+    if not args.no_autotune and args.threads == 0 and args.fft_path == 0 and args.gather_mode == 0 \
+            and args.cluster_set == 0:
         from paper_1711_11407_gb300 import autotune
         p, tuning = autotune.tune(wl.dims, p, cubes, offs, alpha, tau, reps=3, cache_path=None)
     plan = Plan(wl.dims, p)
@@ -655,6 +657,7 @@ def main():
                        "cuda_graph": graph is not None, "parallelism": f"batch sharded over {world} GPU(s), no collective",
                        "threads": plan.info["threads"], "grid": plan.info["grid"], "smem_bytes": plan.info["smem_bytes"],
                        "fft_path": plan.info["fft_path"], "gather_mode": p.gather_mode,
+                       "global_workspace": plan.info["global_workspace"],
                        "autotune_ms": tuning},
             "roofline": roofline, "gpu_launches": args.steps, "exact_support_success": success,
             "mean_iterations": float(np.mean(iters)),

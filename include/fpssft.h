@@ -119,6 +119,14 @@ typedef struct {
                         offsets, schedules and results -- FPS-SFT reads a fraction of each cube, so
                         this moves far fewer bytes when the early stop comes soon; other host memory
                         is copied as with 0 */
+  int cluster_set;   /* where path 3 keeps each signal's recovered set (list and index): 0 (library
+                        choice) or 1 = shared memory when it fits, else plan-owned global workspace;
+                        2 = global workspace (L2-resident) always.  Without the set a CTA needs about
+                        a third of the shared memory, so smaller CTAs (`threads`) can share an SM and
+                        a batch with more clusters than SMs is resident at once -- faster for long
+                        runs with small sets (64 noisy 1024^2 images, 256-thread CTAs), slower for
+                        short runs with large sets (noiseless images), hence an autotuner candidate
+                        rather than the default.  The results do not depend on it */
 } fpssft_params;
 
 typedef struct fpssft_plan_s* fpssft_plan_t;

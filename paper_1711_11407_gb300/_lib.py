@@ -86,7 +86,7 @@ class CParams(ctypes.Structure):
                 ("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("fp64_decisions", ctypes.c_int), ("gather_mode", ctypes.c_int), ("fft_path", ctypes.c_int),
                 ("amp_average", ctypes.c_int), ("radix_plan", ctypes.c_int),
-                ("host_cubes", ctypes.c_int)]
+                ("host_cubes", ctypes.c_int), ("cluster_set", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -32,12 +32,14 @@ class Params:
     amp_average: bool = False
     radix_plan: int = 0
     host_cubes: int = 0
+    cluster_set: int = 0         # path 3: 0 library choice, 1 shared memory when it fits, 2 global workspace
 
     def c(self):
         return _lib.CParams(int(self.T), int(self.k_cap), float(self.theta0), float(self.rho), float(self.eta),
                             int(self.early_stop), int(self.peel_mode), int(self.threads), int(self.ctas_per_sm),
                             int(bool(self.fp64_decisions)), int(self.gather_mode), int(self.fft_path),
-                            int(bool(self.amp_average)), int(self.radix_plan), int(self.host_cubes))
+                            int(bool(self.amp_average)), int(self.radix_plan), int(self.host_cubes),
+                            int(self.cluster_set))
 
 
 @dataclass

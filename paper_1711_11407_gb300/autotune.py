@@ -9,6 +9,8 @@ Candidates are the valid combinations of
                prefetch of the next iteration: throughput over latency) or 5 (4 with the next
                iteration's samples hinted into L2),
   threads      CTA size for paths 1 and 3 (path 2 is fixed at 32 (D+1)),
+  cluster_set  on path 3, the recovered set in shared memory (1) or in global workspace (2; smaller
+               CTAs, more of them resident),
   radix_plan   the order of the shared-memory FFT's mixed-radix stages (paths 1 and 3): tried for
                the fastest of the candidates above, each plan whose stage sequence differs from
                the default for some line length of the batch (fpssft_fft_stages).
@@ -60,7 +62,8 @@ def candidates(dims, params: Params):
             if th > L_max // 2:
                 continue
             for gm in (1, 3):
-                out.append(replace(params, fft_path=3, gather_mode=gm, threads=th))
+                for cs in (1, 2):
+                    out.append(replace(params, fft_path=3, gather_mode=gm, threads=th, cluster_set=cs))
     return out
 
 
@@ -145,6 +148,8 @@ def tune(dims, params: Params, cubes, offsets, alpha, tau, reps=5, cache_path=DE
             out = plan.alloc_output(cubes.device)
             ms = _time(plan, (cubes, offsets, alpha, tau, out), reps, flush)
             desc = f"path={cand.fft_path} gather={cand.gather_mode} threads={plan.info['threads']}"
+            if cand.fft_path == 3:
+                desc += " set=global" if plan.info["global_workspace"] else " set=shared"
             if cand.radix_plan:
                 desc += f" radix_plan={cand.radix_plan}"
             timings[desc] = ms
@@ -157,7 +162,7 @@ def tune(dims, params: Params, cubes, offsets, alpha, tau, reps=5, cache_path=DE
         return params, timings
     run(radix_candidates(dims, best))
     choice = {"fft_path": best.fft_path, "gather_mode": best.gather_mode, "threads": best.threads,
-              "radix_plan": best.radix_plan}
+              "radix_plan": best.radix_plan, "cluster_set": best.cluster_set}
     if cache_path:
         cache[key] = {"choice": choice, "timings": timings}
         try:

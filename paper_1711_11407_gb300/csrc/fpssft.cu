@@ -270,6 +270,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if (!(pr.theta0 >= 0.f) || !(pr.rho >= 0.f) || !(pr.eta >= 0.f)) return fail(FPSSFT_ERR_INVALID, "thresholds must be >= 0");
   if (pr.peel_mode != 0) return fail(FPSSFT_ERR_UNSUPPORTED, "only peel_mode 0 (bins) is implemented on the GPU");
   if (pr.gather_mode < 0 || pr.gather_mode > 5) return fail(FPSSFT_ERR_INVALID, "gather_mode must be in [0, 5]");
+  if (pr.cluster_set < 0 || pr.cluster_set > 2) return fail(FPSSFT_ERR_INVALID, "cluster_set must be in [0, 2]");
   if (pr.fft_path < 0 || pr.fft_path > 3) return fail(FPSSFT_ERR_INVALID, "fft_path must be in [0, 3]");
   if (pr.radix_plan < 0 || pr.radix_plan > 3) return fail(FPSSFT_ERR_INVALID, "radix_plan must be in [0, 3]");
   if (pr.host_cubes < 0 || pr.host_cubes > 1) return fail(FPSSFT_ERR_INVALID, "host_cubes must be 0 or 1");
@@ -426,14 +427,16 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     // the set in shared memory if it fits (with, then without the prefetch buffer), else in
     // global workspace
     const size_t cap = (size_t)optin - static_reserve;
-    bool gs = false;
-    CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c);
+    // cluster_set 2: the set in global workspace even when it fits shared memory (smaller CTAs can
+    // then share an SM: the autotuner's candidate for batches with more clusters than SMs)
+    bool gs = pr.cluster_set == 2;
+    CLayout cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c, gs);
     P->prefetch = pf_c;
     if (cl.total > cap && pf_c) {
-      cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false);
+      cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, false, gs);
       P->prefetch = false;
     }
-    if (cl.total > cap) {
+    if (cl.total > cap && !gs) {
       gs = true;
       cl = recover_layout_c(D, P->L_max, pr.k_cap, 1 << hb, pf_c, true);
       P->prefetch = pf_c;

@@ -33,7 +33,7 @@ def _plan(D, batch, dims, **kw):
     lib = _lib.load()
     p = _lib.CParams(kw.get("T", 10), kw.get("k_cap", 64), kw.get("theta0", 1e-3), 1e-3, 0.05, 1,
                      kw.get("peel_mode", 0), kw.get("threads", 0), 0, 0, kw.get("gather_mode", 0), kw.get("fft_path", 0), 0,
-                     kw.get("radix_plan", 0), kw.get("host_cubes", 0))
+                     kw.get("radix_plan", 0), kw.get("host_cubes", 0), kw.get("cluster_set", 0))
     h = ctypes.c_void_p()
     d = np.ascontiguousarray(np.asarray(dims, np.int64).reshape(-1))
     st = lib.fpssft_plan_create(ctypes.byref(h), D, batch, d.ctypes.data_as(ctypes.c_void_p) if d.size else None,
@@ -57,6 +57,8 @@ def _plan(D, batch, dims, **kw):
     (2, 1, [8, 8], {"radix_plan": -1}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"radix_plan": 4}, _lib.ERR_INVALID),
     (2, 1, [8, 8], {"host_cubes": 2}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"cluster_set": 3}, _lib.ERR_INVALID),
+    (2, 1, [8, 8], {"cluster_set": -1}, _lib.ERR_INVALID),
     (2, 1, [1 << 20, 3], {}, _lib.ERR_UNSUPPORTED),         # D L max N_d >= 2^31
     (2, 1, [65536, 65536], {}, _lib.ERR_UNSUPPORTED),       # N >= 2^31
 ])

@@ -14,6 +14,10 @@ def test_candidates_offer_the_register_path_only_for_eligible_line_lengths():
     assert {x.fft_path for x in c} == {1, 3}
     assert all(x.gather_mode in (1, 2, 3, 4, 5) for x in c)
     assert {x.threads for x in c if x.fft_path == 3} == {256, 512, 1024}
+    # every cluster-path launch is offered with the set in shared memory and in global workspace
+    assert {(x.threads, x.gather_mode, x.cluster_set) for x in c if x.fft_path == 3} == \
+        {(t, g, s) for t in (256, 512, 1024) for g in (1, 3) for s in (1, 2)}
+    assert all(x.cluster_set == 0 for x in c if x.fft_path != 3)
     c = autotune.candidates(np.array([[512, 512]]), p)          # L = 512: no register path
     assert {x.fft_path for x in c} == {1, 3}
     assert {x.threads for x in c if x.fft_path == 3} == {256}

@@ -54,12 +54,11 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("case", sorted(CASES))
-def test_cluster_path_matches_oracle(case):
+def _run_case(case, cluster_set=0):
     from paper_1711_11407_gb300.api import Plan
     make, T, kcap, threads, gm = CASES[case]
     wl = make()
-    kw = dict(k_cap=kcap, fft_path=3, threads=threads, gather_mode=gm)
+    kw = dict(k_cap=kcap, fft_path=3, threads=threads, gather_mode=gm, cluster_set=cluster_set)
     if T is not None:
         kw["T"] = T
     p = configs.params_for(wl, **kw)
@@ -68,6 +67,8 @@ def test_cluster_path_matches_oracle(case):
     assert plan.info["grid"] == wl.batch * (wl.D + 1)
     if threads:
         assert plan.info["threads"] == threads
+    if cluster_set == 2:
+        assert plan.info["global_workspace"] == 1
     out = plan.recover(*to_dev(wl))
     torch.cuda.synchronize()
     for b in range(wl.batch):
@@ -77,6 +78,51 @@ def test_cluster_path_matches_oracle(case):
         assert_same_set(k, a, ref, f"{case} signal {b} dims {wl.dims[b]}")
         assert int(out.iters[b]) == ref.iters, f"iterations {int(out.iters[b])} vs oracle {ref.iters}"
         assert int(out.status[b]) == ref.status
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_cluster_path_matches_oracle(case):
+    _run_case(case)
+
+
+@pytest.mark.parametrize("case", ["D2_240x256_256thr_prefetch", "D2_1024_noiseless", "D3_24x32x40", "D4_4x6x8x10",
+                                  "D2_mixed_lengths"])
+def test_cluster_path_with_the_set_in_global_workspace_matches_oracle(case):
+    """cluster_set 2: each signal's list and index in plan-owned global workspace (L2-resident)
+    instead of shared memory; the oracle's sets, iteration counts and statuses."""
+    _run_case(case, cluster_set=2)
+
+
+def test_set_in_global_workspace_keeps_a_batch_larger_than_the_gpu_resident_and_equal():
+    """More clusters than SMs (1024-point lines): with the sets in global workspace and 256-thread
+    CTAs two CTAs share an SM and the whole batch is resident at once; the sets equal those of the
+    library's shared-memory layout and, on a sample, the oracle's."""
+    from paper_1711_11407_gb300.api import Plan
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    wl = S.make_workload("images_1024x1024", batch=sms // 3 + 2, snr_db=None)
+    auto = Plan(wl.dims, configs.params_for(wl, fft_path=3, cluster_set=2, threads=256))
+    assert auto.info["global_workspace"] == 1 and auto.info["threads"] == 256
+    shared = Plan(wl.dims, configs.params_for(wl))
+    assert shared.info["fft_path"] == 3 and shared.info["global_workspace"] == 0 and shared.info["threads"] == 512
+    few = Plan(wl.dims[:8], configs.params_for(wl, fft_path=3, cluster_set=1))
+    assert few.info["global_workspace"] == 0 and few.info["threads"] == 512
+    args = to_dev(wl)
+    a = auto.recover(*args)
+    b = shared.recover(*args)
+    torch.cuda.synchronize()
+    assert torch.equal(a.count, b.count) and torch.equal(a.iters, b.iters) and torch.equal(a.status, b.status)
+    for s in range(wl.batch):
+        n = int(a.count[s])
+        assert torch.equal(a.k[s, :n], b.k[s, :n])
+        assert torch.allclose(a.a[s, :n], b.a[s, :n], rtol=AMP_TOL, atol=0)
+    p = configs.params_for(wl)
+    for s in (0, wl.batch - 1):
+        Tb = int(auto.T[s])
+        ref = O.recover(wl.cube(s), wl.alpha[s, :Tb], wl.tau[s, :Tb], oracle_params(p, Tb))
+        k, aa = a.signal(s)
+        assert_same_set(k, aa, ref, f"signal {s}")
+    for pl in (auto, shared, few):
+        pl.close()
 
 
 def test_cluster_path_equals_the_one_cta_per_signal_path():
