@@ -86,16 +86,16 @@ typedef struct {
                         FP32 and re-evaluate in FP64 only the bins whose FP32 value falls inside a
                         guard band around a threshold -- the verdicts are the same either way */
   int gather_mode;   /* line-sample loads of fpssft_recover: 0 = library choice (synchronous
-                        through L1, except mode 3 on path 3 for L_max < 2048), 1 = synchronous through L1,
+                        through L1, except mode 3 on path 3 for L_max < 2048 and on the register-FFT
+                        path for batches its mode-3 kernel holds resident at once, and mode 4 on the
+                        register-FFT path for larger batches), 1 = synchronous through L1,
                         2 = synchronous cached in L2 only, 3 = asynchronous copies (cp.async) of the
                         next iteration's lines into a shared-memory buffer while the current one
                         computes.  On the register-FFT path modes 1 and 2 prefetch the next
                         iteration into registers instead; 4 = synchronous through L1 with no
-                        prefetch (on the register-FFT path the library's choice when the batch has
-                        more signals than resident CTAs; elsewhere the same as 1); 5 = as 4, with the
+                        prefetch (register-FFT path; elsewhere the same as 1); 5 = as 4, with the
                         next iteration's samples hinted into L2 (prefetch.global.L2) right after the
-                        FFT (register-FFT path: the library's choice for batches that fit the
-                        resident CTAs; elsewhere the same as 1) */
+                        FFT (register-FFT path; elsewhere the same as 1) */
   int fft_path;      /* fpssft_recover's kernel: 0 = library choice, 1 = one CTA per signal with the
                         shared-memory mixed-radix FFT (any L), 2 = one warp per line with a register
                         FFT (every L of the batch in {32, 64, 128, 256}), 3 = one CTA per line, the

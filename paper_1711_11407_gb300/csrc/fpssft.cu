@@ -563,12 +563,30 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
     if (per_sm < 1) return fail(FPSSFT_ERR_UNSUPPORTED, "recovery kernel cannot be resident with this CTA size / shared memory");
     if (P->p.ctas_per_sm > 0) per_sm = std::min(per_sm, P->p.ctas_per_sm);
     P->grid = std::max(1, std::min(batch, per_sm * P->sm_count));
-    // register path, library choice: with more signals than resident CTAs no prefetch (the other
-    // CTAs hide the gather's latency; throughput), else the next iteration hinted into L2 (latency)
+    // register path, library choice: a batch that the staged-prefetch kernel holds resident at once
+    // (latency-bound: a few signals per SM) has each iteration's successor copied into shared memory
+    // by cp.async while the current one computes; a larger batch gets no prefetch (throughput: the
+    // other CTAs hide the gather's latency)
     if (P->warp_path && P->p.gather_mode == 0) {
-      P->warp_mode = batch > P->grid ? kWNone : kWL2Hint;
-      e2 = ensure_dynamic_smem(warp_kfn(P->warp_mode), P->smem);
-      if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
+      const size_t smem_st = recover_layout_w(DD, P->L_max, P->p.k_cap, true).total;
+      int per_sm_st = 0;
+      if (smem_st + static_reserve <= (size_t)optin) {
+        e2 = ensure_dynamic_smem(warp_kfn(kWStaged), smem_st);
+        if (e2 == cudaSuccess)
+          e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_st, warp_kfn(kWStaged), P->threads, smem_st);
+        if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("staged recovery kernel: ") + cudaGetErrorString(e2));
+        if (P->p.ctas_per_sm > 0) per_sm_st = std::min(per_sm_st, P->p.ctas_per_sm);
+      }
+      if (per_sm_st >= 1 && (long long)batch <= (long long)per_sm_st * P->sm_count) {
+        P->warp_mode = kWStaged;
+        P->smem = smem_st;
+        P->prefetch = true;
+        P->grid = std::max(1, batch);
+      } else {
+        P->warp_mode = kWNone;
+        e2 = ensure_dynamic_smem(warp_kfn(P->warp_mode), P->smem);
+        if (e2 != cudaSuccess) return fail(FPSSFT_ERR_CUDA, std::string("cudaFuncSetAttribute(recovery kernel): ") + cudaGetErrorString(e2));
+      }
     }
     if (P->cluster_path) P->grid = batch * (DD + 1);   // one cluster per signal, not persistent
     if (P->cluster_gs) {   // one slice of global workspace per signal

@@ -258,7 +258,9 @@ __device__ __forceinline__ int iterate_w(const RecoverArgs& A, const Shape& sh, 
 #endif
 
 #ifndef FPSSFT_WS_THREADS_PER_SM
-#define FPSSFT_WS_THREADS_PER_SM 768   // same for the variant that stages the prefetch in shared memory
+// same for the variant that stages the prefetch in shared memory, the latency variant: a generous
+// budget (no spills; 768 threads per SM spilled and ran 1.6x slower on 256 noisy 64^3 cubes)
+#define FPSSFT_WS_THREADS_PER_SM 384
 #endif
 
 template <int D, int WM>
