@@ -103,10 +103,13 @@ def main(argv=None):
     ap.add_argument("--noiseless", action="store_true", help="drop the workload's noise")
     ap.add_argument("--fft-path", type=int, default=None)
     ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--gather-mode", type=int, default=None)
+    ap.add_argument("--cluster-set", type=int, default=None)
     ap.add_argument("--dump", default=None, help="save the last launch's output (.npz)")
     a = ap.parse_args(argv)
     _lib.use_library(build_variant())
-    over = {k: v for k, v in (("fft_path", a.fft_path), ("threads", a.threads)) if v is not None}
+    over = {k: v for k, v in (("fft_path", a.fft_path), ("threads", a.threads), ("gather_mode", a.gather_mode),
+                              ("cluster_set", a.cluster_set)) if v is not None}
     res = run(a.workload, batch=a.batch, reps=a.reps, snr_db=None if a.noiseless else "default", dump=a.dump, **over)
     print(json.dumps(res))
 
