@@ -516,6 +516,7 @@ extern "C" fpssft_status fpssft_plan_create(fpssft_plan_t* out, int D, int batch
   if ((e = cudaMalloc(&P->d_order, nb * sizeof(int))) != cudaSuccess) return cleanup_fail("cudaMalloc order", e);
   if ((e = cudaMalloc(&P->d_twiddles, std::max<size_t>(1, tw_pool.size()) * sizeof(float2))) != cudaSuccess) return cleanup_fail("cudaMalloc twiddles", e);
   if ((e = cudaMalloc(&P->d_counter, sizeof(int))) != cudaSuccess) return cleanup_fail("cudaMalloc counter", e);
+  if ((e = cudaMemset(P->d_counter, 0, sizeof(int))) != cudaSuccess) return cleanup_fail("clear counter", e);
   if (batch > 0) {
     if ((e = cudaMemcpy(P->d_shapes, P->shapes.data(), P->shapes.size() * sizeof(Shape), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload shapes", e);
     if ((e = cudaMemcpy(P->d_sig_shape, P->sig_shape.data(), batch * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail("upload sig_shape", e);
@@ -721,14 +722,14 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   if (!cubes || !offsets || !alpha || !tau || !out_k || !out_a || !out_count || !out_iters || !out_status)
     return fail(FPSSFT_ERR_INVALID, "null device pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  RecoverArgs A;
+  RecoverArgs A{};
   A.cubes = static_cast<const float2*>(cubes);
   A.offsets = offsets;
   A.alpha = alpha;
   A.tau = tau;
   A.sched_stride = P->T_max * P->D;
   A.tab = P->tables();
-  A.work_counter = P->d_counter;
+  A.work_counter = P->d_counter;        // zero at plan creation, returned to 0 by every launch
   A.batch = P->batch;
   A.k_cap = P->p.k_cap;
   A.hash_bits = P->hash_bits;
@@ -746,7 +747,6 @@ extern "C" fpssft_status fpssft_recover(fpssft_plan_t P, const void* cubes, cons
   A.out_count = out_count;
   A.out_iters = out_iters;
   A.out_status = out_status;
-  FPSSFT_CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
   return dispatch_D(P->D, [&](auto Dc) -> fpssft_status {
     constexpr int DD = decltype(Dc)::value;
     if (P->warp_path) {

@@ -28,7 +28,7 @@ struct RecoverArgs {
   const int* tau;
   int sched_stride;          // T_max * D
   DeviceTables tab;
-  int* work_counter;
+  int* work_counter;         // 0 at launch; the launch's last claim returns it to 0 (claim_signal)
   int batch;
   int k_cap;
   int hash_bits;
@@ -47,6 +47,16 @@ struct RecoverArgs {
   int* out_iters;
   int* out_status;
 };
+
+// Next queue position for a persistent recovery CTA (thread 0).  Every CTA claims until it draws a
+// position past the batch, so a launch hands out exactly batch + gridDim.x positions; whoever draws
+// the last one knows every claim of the launch has been made and returns the counter to 0, so the
+// next launch on the stream needs no reset of its own.
+__device__ __forceinline__ int claim_signal(const RecoverArgs& A) {
+  const int c = atomicAdd(A.work_counter, 1);
+  if (c == A.batch + (int)gridDim.x - 1) atomicExch(A.work_counter, 0);
+  return c;
+}
 
 struct SmemLayout {
   size_t bufA, bufB, bufC, tw, stw, la, lk, lkey, hkey, hidx, total;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 512 && D <= 2) ? 2 : 1) k_recov
 
   int loaded = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
+    if (threadIdx.x == 0) s_sig = claim_signal(A);
     __syncthreads();
     const int qi = s_sig;
     if (qi >= A.batch) break;

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(32 * (D + 1), (WM == kWStaged ? FPSSFT_WS_THRE
 
   int loaded = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_sig = atomicAdd(A.work_counter, 1);
+    if (threadIdx.x == 0) s_sig = claim_signal(A);
     __syncthreads();
     const int qi = s_sig;
     if (qi >= A.batch) break;
