@@ -202,7 +202,10 @@ fpssft_status fpssft_lines(fpssft_plan_t plan, const void* cubes, const int64_t*
  *                row-major linear frequency index.
  *   out_iters:   iterations whose lines were sampled.
  *   out_status:  FPSSFT_OK or FPSSFT_ERR_CAPACITY per signal.
- * Allocates nothing; the caller's buffers and the plan's workspace are the only memory used.
+ * Allocates nothing; the caller's buffers and the plan's workspace are the only memory used.  One
+ * kernel launch and nothing else is enqueued: the plan's work counter is zero when the plan is
+ * created and every launch returns it to zero, so launches of one plan must be ordered (one stream,
+ * or events between streams).
  * `cubes` may also point to pinned (page-locked, mapped) host memory: the gather then reads the
  * samples it needs over the host link (on GB300 the cache-coherent NVLink-C2C) instead of the
  * caller copying every cube to the device first. */
