@@ -136,3 +136,17 @@ def test_e2e_self_check_compares_whole_sets_not_counts():
     o = out()
     o.iters[1] = 5
     assert not bench.same_sets(ref, o)
+
+
+def test_cpu_baseline_repeats_the_signals_of_a_workload_smaller_than_the_core_count():
+    """A workload with fewer signals than host cores (a single image, say) is timed with one core
+    per signal, each recovering its signal over and over until the round takes a second, so that the
+    pool's start-up and hand-over do not dominate a few milliseconds of oracle work."""
+    from paper_1711_11407_gb300 import configs, synth
+    if len(os.sched_getaffinity(0)) < 3:
+        import pytest
+        pytest.skip("needs at least 3 host cores")
+    wl = synth.make_workload("uneven_2d", batch=2, shapes=[(16, 16)], K=lambda N: 4, T=6)
+    rate, n, wall, cores = bench.oracle_rate(wl, configs.params_for(wl), 12.0, [0, 1])
+    assert cores == 2 and wall >= 1.0
+    assert n % 2 == 0 and n >= 4 and rate == n / wall
