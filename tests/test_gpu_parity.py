@@ -841,3 +841,65 @@ def test_decode_applies_magnitude_and_grid_tolerances_like_the_oracle(fp64):
         if accept:
             assert tuple(kk[b, 0].tolist()) == ref[0][1] == (1, 1), name
     plan.close()
+
+
+def test_register_path_library_choice_stages_resident_batches_only():
+    """gather_mode 0 on the register path: a batch the staged-prefetch kernel holds resident at once
+    gets the cp.async prefetch, a larger one none; either way the sets are those of the explicit
+    modes and, on a sample, the oracle's."""
+    from paper_1711_11407_gb300.api import Plan
+    small = S.make_workload("uneven_2d", batch=64)
+    large = S.make_workload("uneven_2d", batch=4096, shapes=[(64, 64)])
+    for wl, staged in ((small, True), (large, False)):
+        p = configs.params_for(wl)
+        plan = Plan(wl.dims, p)
+        assert plan.info["fft_path"] == 2 and plan.info["prefetch"] == (1 if staged else 0)
+        out = plan.recover(*to_dev(wl))
+        explicit = Plan(wl.dims, configs.params_for(wl, gather_mode=3 if staged else 4))
+        ref = explicit.recover(*to_dev(wl))
+        torch.cuda.synchronize()
+        assert torch.equal(out.count, ref.count) and torch.equal(out.iters, ref.iters)
+        for b in range(wl.batch):
+            n = int(out.count[b])
+            assert torch.equal(out.k[b, :n], ref.k[b, :n])
+            assert torch.allclose(out.a[b, :n], ref.a[b, :n], rtol=AMP_TOL, atol=0)
+        for b in (0, wl.batch - 1):
+            T = int(plan.T[b])
+            o = O.recover(wl.cube(b), wl.alpha[b, :T], wl.tau[b, :T], oracle_params(p, T))
+            k, a = out.signal(b)
+            assert_same_set(k, a, o, f"signal {b}")
+        plan.close()
+        explicit.close()
+
+
+def test_persistent_launches_replayed_back_to_back_give_the_same_sets():
+    """More signals than resident CTAs, so every CTA claims several signals from the plan's work
+    counter; the launch leaves that counter at zero for the next one (no reset is enqueued), so
+    replaying the same launch from a CUDA graph gives the first launch's sets every time."""
+    from paper_1711_11407_gb300.api import Plan
+    wl = S.make_workload("uneven_2d", batch=3000, shapes=[(64, 64), (128, 128)])
+    plan = Plan(wl.dims, configs.params_for(wl))
+    assert plan.info["grid"] < wl.batch
+    args = to_dev(wl)
+    first = plan.recover(*args)
+    torch.cuda.synchronize()
+    keep = {f: getattr(first, f).clone() for f in ("k", "a", "count", "iters", "status")}
+    out = plan.alloc_output(torch.device("cuda:0"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.recover(*args, out=out, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.recover(*args, out=out, stream=s)
+    for _ in range(3):
+        out.count.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out.count, keep["count"]) and torch.equal(out.iters, keep["iters"])
+        assert torch.equal(out.status, keep["status"])
+        for b in range(0, wl.batch, 97):
+            n = int(keep["count"][b])
+            assert torch.equal(out.k[b, :n], keep["k"][b, :n])
+    plan.close()
