@@ -157,3 +157,38 @@ def test_fft_stage_sequences_multiply_to_L_in_the_plan_order(plan):
         if plan == 0:
             assert sum(v in (2, 4) for v in r) <= 1
     assert lib.fpssft_fft_stages(64, 5, out, ctypes.byref(n)) == _lib.ERR_INVALID
+
+
+def _header_fields(struct_name):
+    """(type, name) of every member of `typedef struct { ... } struct_name;` in include/fpssft.h."""
+    text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fpssft.h")).read()
+    end = text.index("} " + struct_name + ";")
+    start = text.rindex("typedef struct {", 0, end)
+    body = re.sub(r"/\*.*?\*/", "", text[start:end], flags=re.S)
+    return re.findall(r"^\s*(int|float)\s+(\w+)\s*;", body, flags=re.M)
+
+
+@pytest.mark.parametrize("struct_name,cls", [("fpssft_params", "CParams"), ("fpssft_plan_info", "PlanInfo")])
+def test_ctypes_structs_match_the_header(struct_name, cls, tmp_path):
+    """The binding's ctypes structs declare the header's members in the header's order and types,
+    and a C compiler lays the header's struct out at the same offsets and size."""
+    import shutil
+    import subprocess
+    klass = getattr(_lib, cls)
+    fields = _header_fields(struct_name)
+    ctype = {"int": ctypes.c_int, "float": ctypes.c_float}
+    assert [(n, ctype[t]) for t, n in fields] == [(n, t) for n, t in klass._fields_]
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fpssft.h"\nint main(void) {\n'
+                   + f'  printf("%zu\\n", sizeof({struct_name}));\n'
+                   + "".join(f'  printf("%zu\\n", offsetof({struct_name}, {n}));\n' for _, n in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(klass)
+    assert got[1:] == [getattr(klass, n).offset for _, n in fields]
