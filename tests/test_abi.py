@@ -192,3 +192,13 @@ def test_ctypes_structs_match_the_header(struct_name, cls, tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got[0] == ctypes.sizeof(klass)
     assert got[1:] == [getattr(klass, n).offset for _, n in fields]
+
+
+def test_binding_signatures_take_as_many_arguments_as_the_header_prototypes():
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "fpssft.h")).read(), flags=re.S)
+    protos = dict(re.findall(r"\b(fpssft_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S))
+    assert set(protos) == set(_lib.SIGNATURES)
+    for name, params in protos.items():
+        params = " ".join(params.split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert n == len(_lib.SIGNATURES[name][1]), f"{name}: header takes {n} arguments"
